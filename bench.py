@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the Fisher-vector encoder on one 320x240-shaped frame.
+
+Workload (the paper's video frame, Sec. 4: K=256 components, dense
+descriptors at stride 4 over an 8-scale pyramid of a 320x240 frame, stood in
+for by seeded synthetic data): N=19200 descriptors of D=64 per frame, 80%
+drawn from the GMM and 20% Uniform(-3,3) outliers; GMM w ~ Dirichlet(1),
+mu ~ N(0,1), sigma^2 ~ U(0.1,1).
+
+A step encodes every frame of a pool of 64 distinct frames (315 MB of FP32
+descriptors, larger than the 129 MB L2) one frame per fv_encode call, the
+whole hot path per frame: posteriors, statistics, per-range reduction,
+scalings, signed square root and L2.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1604_03498_gb300 import synth  # noqa: E402
+
+K_COMP, D_DIM, N_DESC = 256, 64, 19200
+POOL = 64
+GMM_SEED = 0
+METRIC = "FV descriptors/sec (320x240-shaped frames, N=19200, D=64, K=256)"
+WORKLOAD = "one 320x240-shaped frame per encode: N=19200 descriptors, D=64, K=256 diagonal GMM"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def make_pool(rank: int, n_frames: int):
+    w, mu, var = synth.make_gmm(K_COMP, D_DIM, seed=GMM_SEED)
+    frames = [synth.sample_descriptors(w, mu, var, N_DESC, seed=10_000 * (rank + 1) + i, gmm_frac=0.8)
+              for i in range(n_frames)]
+    return w, mu, var, frames
+
+
+# ---- clocks sampled during the timed region --------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            if self.uuid and self.uuid not in p[0]:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- oracle on the host cores ------------------------------------------------------------
+def oracle_throughput(frames, w, mu, var, seconds: float, rows: int | None = None):
+    """Run the FP64 oracle as it stands on every host core (one frame per thread,
+    ctypes releases the GIL) for about `seconds`; returns (desc/s, cores, sample)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rows = rows or N_DESC
+    done = 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        i = 0
+        while True:
+            batch = [frames[(i + j) % len(frames)][:rows] for j in range(cores)]
+            i += cores
+            list(ex.map(lambda X: oracle.encode(X, w, mu, var), batch))
+            done += rows * cores
+            if time.perf_counter() - t0 >= seconds:
+                break
+    dt = time.perf_counter() - t0
+    sample = f"{done // rows} frames x {rows} descriptors on {cores} threads, {dt:.1f} s"
+    return done / dt, cores, sample
+
+
+def run_reference(args):
+    """The oracle as the reference arm, same workload, metric and unit."""
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return 0
+    w, mu, var, frames = make_pool(0, 16)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # calibrate the per-step sample so that steps + warmup end within ~2 minutes
+    t0 = time.perf_counter()
+    oracle.encode(frames[0][:500], w, mu, var)
+    per_row = (time.perf_counter() - t0) / 500
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rows = int(max(200, min(N_DESC, budget / per_row)))
+
+    def step(i):
+        batch = [frames[(i * cores + j) % len(frames)][:rows] for j in range(cores)]
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda X: oracle.encode(X, w, mu, var), batch))
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = args.steps * cores * rows / dt
+    sample = f"each step {cores} frames x {rows} descriptors (one per thread)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "descriptors/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (FP64 CPU oracle)", "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "descriptors/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "descriptors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---- measured traffic of a kernel (from a committed ncu summary) ------------------
+def measured_traffic(kernel: str, source: str):
+    """DRAM bytes per launch recorded in profiles/traffic.md for `kernel`, valid
+    only while the kernel's source file still has the hash recorded there."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    src = os.path.join(ROOT, "paper_1604_03498_gb300", "csrc", source)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    for ln in open(path):
+        m = re.match(r"\|\s*(\S+)\s*\|\s*(\w+)\s*\|\s*([0-9.eE+]+)\s*\|", ln)
+        if m and m.group(1) == kernel and m.group(2) == sha:
+            return float(m.group(3))
+    return None
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1604_03498_gb300 import fv
+
+    rank, local_rank, world = _env_rank()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w, mu, var, frames = make_pool(rank, POOL)
+    g = fv.fv_gmm_load(w, mu, var, fv.FV_PREC_FP32)
+    Xd = torch.from_numpy(np.stack(frames)).cuda()             # [POOL][N][D] resident in HBM
+    out = torch.zeros(POOL, 2 * K_COMP * D_DIM, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for f in range(POOL):
+            fv.fv_encode(g, Xd[f], out[f], allow=(fv.FV_OK,))
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    n0 = fv.fv_launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = fv.fv_launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    desc = world * args.steps * POOL * N_DESC
+    value = desc / (ms / 1e3)
+
+    # per-kernel device time over the same number of steps (events on the launch stream)
+    fv.fv_prof_enable(True)
+    fv.fv_prof_collect()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = fv.fv_prof_collect()
+    fv.fv_prof_enable(False)
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kname, (klaunch, kms) = top
+    per_launch_s = kms / klaunch / 1e3
+    peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 FMA lanes x 2 flop x max clock
+    work = {  # algorithmic FP32 flops per launch (one frame): see the design doc
+        "f32_posteriors": 4.0 * K_COMP * D_DIM * N_DESC,
+        "f32_stats": 6.0 * K_COMP * D_DIM * N_DESC,
+    }
+    roofline = None
+    if kname in work:
+        achieved = work[kname] / per_launch_s / 1e12
+        roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": measured_traffic(kname, "fv_fp32.cu"),
+                    "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                    "launch_ms": per_launch_s * 1e3,
+                    "share": kms / sum(v[1] for v in prof.values())}
+    kernels = {k: {"launches": v[0], "ms_per_launch": v[1] / max(1, v[0])} for k, v in prof.items()}
+
+    # end to end through the C ABI with pinned host buffers (H2D + D2H inside)
+    Xh = torch.from_numpy(np.stack(frames)).pin_memory()
+    outh = torch.zeros(POOL, 2 * K_COMP * D_DIM).pin_memory()
+    e2e_steps = max(1, min(args.steps, 20))
+    for f in range(4):
+        fv.fv_encode(g, Xh[f], outh[f], allow=(fv.FV_OK,))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for f in range(POOL):
+            fv.fv_encode(g, Xh[f], outh[f], allow=(fv.FV_OK,))
+    dt = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    e2e = {"value": world * e2e_steps * POOL * N_DESC / dt, "unit": "descriptors/s",
+           "h2d_bytes_per_step": POOL * N_DESC * D_DIM * 4, "d2h_bytes_per_step": POOL * 2 * K_COMP * D_DIM * 4,
+           "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, cores, sample = oracle_throughput(frames, w, mu, var, args.cpu_seconds)
+        cpu = {"value": v, "unit": "descriptors/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "descriptors/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (plain FP32 form)", "frames_per_step": POOL,
+                       "frames_per_s": value / N_DESC, "us_per_frame": 1e3 * ms / (args.steps * POOL),
+                       "l2": "inputs larger than L2: 64-frame pool = 315 MB", "parallelism": f"dp{world} (frames)"},
+            "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "e2e": e2e,
+            "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line))
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * fv.h - C ABI of the GB300 Fisher-vector encoder.
+ *
+ * The library encodes sets of local descriptors against a diagonal-covariance
+ * Gaussian mixture model into improved Fisher vectors, as stated in
+ * "GPU-FV: Realtime Fisher Vector and Its Applications in Video Monitoring"
+ * (Ma et al., ICMR 2016):
+ *   - the problem statement, Sec. 3.1 and Algorithm 1: inputs are the
+ *     descriptors and the GMM (means, "covariances" = diagonal variances,
+ *     priors), output the Fisher vector {U, V};
+ *   - posteriors (Algorithm 1 first loop; Algorithm 2 on the GPU);
+ *   - first/second-order statistics U, V (Algorithm 1 second loop;
+ *     Algorithm 3 with per-block copies and a reduction kernel);
+ *   - the encoding scheme of Sec. 4 ("the same encoding scheme as VLFeat"):
+ *     u_kd = U_kd / (N sqrt(w_k)), v_kd = V_kd / (N sqrt(2 w_k)), then the
+ *     signed square root and L2 normalisation of z = [u; v].
+ *
+ * Notation: N descriptors of dimension D, K mixture components.
+ * Fisher-vector layout (2*K*D floats): [u_0 .. u_{K-1}, v_0 .. v_{K-1}],
+ * each u_k / v_k block D-contiguous. The paper writes the vector as {V, U};
+ * the order here is a fixed permutation and is documented as such.
+ *
+ * Conventions for every call:
+ *   - every entry point returns an fv_status and never aborts; on error
+ *     fv_last_error() gives a thread-local message;
+ *   - the caller owns all input and output buffers; the library copies what
+ *     it keeps (the GMM at load time, submitted frames at submit time);
+ *   - "on_device" flags say whether a pointer is device memory (1) or host
+ *     memory (0). Host buffers may be pageable; pinned ones copy faster;
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ *     Device work is ordered on it. A call returns only after the result is
+ *     in a host output buffer; with device outputs it returns as soon as the
+ *     work is queued;
+ *   - a GMM handle is immutable after load and may be shared by threads;
+ *   - N == 0 gives FV_ERR_EMPTY and a zero-filled Fisher vector.
+ */
+#ifndef FV_H_
+#define FV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FV_API __attribute__((visibility("default")))
+#else
+#define FV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FV_OK = 0,
+    FV_PENDING = 1,           /* fv_server_poll: result not ready yet */
+    FV_ERR_INVALID = -1,      /* bad argument or GMM parameter */
+    FV_ERR_OOM = -2,          /* device or host allocation failed */
+    FV_ERR_CUDA = -3,         /* a CUDA call failed */
+    FV_ERR_BUSY = -4,         /* server admission refused (slots or memory) */
+    FV_ERR_TIMEOUT = -5,      /* poll deadline passed */
+    FV_ERR_NOTFOUND = -6,     /* unknown ticket */
+    FV_ERR_EMPTY = -7,        /* N == 0: output is zero-filled */
+    FV_ERR_DEVICE = -8,       /* a kernel reported an error flag */
+    FV_ERR_UNSUPPORTED = -9   /* shape outside the implemented limits */
+} fv_status;
+
+typedef enum {
+    FV_PREC_FP32 = 0,  /* plain FP32 form: SIMT kernels, centred statistics */
+    FV_PREC_BF16 = 1   /* precision form: BF16 tensor-core GEMMs, hi+lo split */
+} fv_precision;
+
+/* GMM parameters, all host memory, float32:
+ *   weights   K priors w_k > 0 with |sum_k w_k - 1| <= 1e-5 (renormalised in
+ *             FP64 on load),
+ *   means     K x D row-major mu_kd (finite),
+ *   variances K x D row-major diagonal sigma^2_kd > 0 (finite).
+ * Source: the GMM model "means, covariances, priors" of Algorithm 1. */
+typedef struct {
+    int K;
+    int D;
+    const float *weights;
+    const float *means;
+    const float *variances;
+} fv_gmm_desc;
+
+typedef struct fv_gmm fv_gmm;
+typedef struct fv_server fv_server;
+
+/* Load a GMM onto the current CUDA device and precompute, once and in FP64,
+ * everything the encoder needs (the "compute sqrt(sigma^-1)" step of
+ * Algorithm 1, run by "a simple GPU kernel" per Sec. 3.2): 1/sigma, the
+ * per-component log-constants, 1/sqrt(w), 1/sqrt(2w), and for FV_PREC_BF16
+ * the hi+lo split operand images. Copies every input; *out owns device
+ * memory until fv_gmm_free. Errors: FV_ERR_INVALID (parameter checks above),
+ * FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_UNSUPPORTED (K or D beyond the limits of
+ * the chosen precision, see fv_limits). */
+FV_API int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_gmm **out);
+
+/* Free a handle from fv_gmm_load (NULL is a no-op). The caller must make sure
+ * no queued work still uses it (synchronise the streams it was used on). */
+FV_API void fv_gmm_free(fv_gmm *gmm);
+
+/* Report K, D and precision of a loaded GMM (any pointer may be NULL). */
+FV_API int fv_gmm_info(const fv_gmm *gmm, int *K, int *D, int *precision);
+
+/* Largest K and D the given precision supports. */
+FV_API int fv_limits(fv_precision precision, int *max_K, int *max_D);
+
+/* Encode one descriptor set (Algorithm 1 end to end).
+ *   X        N x D float32 row-major descriptors (host or device),
+ *   fv_out   2*K*D float32 normalised Fisher vector (host or device).
+ * With an FV_PREC_BF16 handle the descriptors are rounded to bfloat16 on the
+ * device before encoding. Scratch is taken stream-ordered from the device's
+ * default memory pool and returned before the call's work ends.
+ * Errors: FV_ERR_INVALID, FV_ERR_EMPTY (N == 0; fv_out zero-filled),
+ * FV_ERR_OOM, FV_ERR_CUDA. */
+FV_API int fv_encode(const fv_gmm *gmm, const float *X, int64_t N, int x_on_device,
+              float *fv_out, int out_on_device, void *cuda_stream);
+
+/* Encode B descriptor sets packed back to back (frame b owns rows
+ * offsets[b] .. offsets[b+1]-1 of X_packed, offsets[0] == 0) in one pass:
+ * one set of kernels over every frame, frames of uneven size sharing the GPU.
+ *   offsets  B+1 int64, HOST memory, non-decreasing,
+ *   fv_out   B x 2*K*D float32.
+ * Empty frames get a zero vector; the call still returns FV_OK when at least
+ * one frame is non-empty, else FV_ERR_EMPTY. */
+FV_API int fv_encode_batch(const fv_gmm *gmm, const float *X_packed, const int64_t *offsets, int B,
+                    int x_on_device, float *fv_out, int out_on_device, void *cuda_stream);
+
+/* Precision form with descriptors already stored as bfloat16 on the device
+ * (uint16 bit patterns, row pitch ld_x >= D elements, ld_x a multiple of 8).
+ * Otherwise as fv_encode_batch; gmm must be an FV_PREC_BF16 handle and X,
+ * fv_out device pointers. offsets is a host array. */
+FV_API int fv_encode_batch_bf16(const fv_gmm *gmm, const uint16_t *X_bf16, int64_t ld_x,
+                         const int64_t *offsets, int B, float *fv_out, void *cuda_stream);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+FV_API const char *fv_last_error(void);
+
+/* ---- instrumentation (not part of the method) -------------------------------
+ * While enabled, every kernel launch of the library is bracketed by two CUDA
+ * events recorded on the stream it is launched on; fv_prof_collect waits for
+ * the recorded events, returns per-kernel launch counts and summed device
+ * time, and clears them. fv_launch_count counts every kernel launched by the
+ * library since it was loaded, profiling or not. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} fv_kernel_stat;
+
+FV_API int fv_prof_enable(int on);
+FV_API int fv_prof_collect(fv_kernel_stat *out, int max, int *n_out);
+FV_API int64_t fv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FV_H_ */

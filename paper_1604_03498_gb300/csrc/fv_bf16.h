@@ -1,0 +1,18 @@
+// Internal declarations of the BF16 (tensor-core) form of the encoder.
+#pragma once
+
+#include "fv_internal.h"
+
+namespace fv {
+
+// Rows per statistics range for the BF16 statistics kernel.
+int64_t bf16_rows_per_range(const fv_gmm *g, int64_t rows, int sms);
+
+// FP32 descriptors (rows x D) -> bfloat16 rows of pitch Dp (zero padded).
+cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, uint16_t *Xb, cudaStream_t st);
+
+// Posteriors and statistics of the BF16 form; returns an fv_status.
+int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
+                     const StatUnit *units, int n_units, float *part, int P, int sms, cudaStream_t st);
+
+}  // namespace fv

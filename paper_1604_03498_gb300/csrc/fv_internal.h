@@ -1,0 +1,112 @@
+// Internal declarations shared by the CUDA translation units of the encoder.
+// Nothing here is part of the public ABI (include/fv.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fv.h"
+
+namespace fv {
+
+// ---- error reporting -------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int status, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define FV_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return ::fv::cuda_fail(e_, #expr); \
+    } while (0)
+
+// ---- instrumentation: launch counting and optional per-kernel event timing --
+// Construct one KernelTimer right before each kernel launch and let it go out
+// of scope right after: it counts the launch and, while profiling is enabled,
+// records start/stop events on the launch stream.
+class KernelTimer {
+  public:
+    KernelTimer(const char *name, cudaStream_t st);
+    ~KernelTimer();
+  private:
+    int slot_;
+    cudaStream_t st_;
+};
+
+// ---- limits ----------------------------------------------------------------
+constexpr int kMaxK_F32 = 512;    // posteriors keep a BM x Kp row block in shared memory
+constexpr int kMaxD_F32 = 1024;
+constexpr int kMaxK_BF16 = 512;   // one 128-lane x K-column TMEM accumulator
+constexpr int kMaxD_BF16 = 80;    // stats GEMM N = 3D + 16 <= 256
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+inline int64_t round_up64(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ---- GMM handle ------------------------------------------------------------
+// Per-component operands, all computed on the device in FP64 from the FP32
+// inputs by the preparation kernel (Algorithm 1, "compute sqrt(sigma^-1)").
+struct GmmDev {
+    // FP32 form
+    float *s_t;      // [D][Kp]  1/sigma, component-contiguous (posteriors)
+    float *nms_t;    // [D][Kp]  -mu/sigma
+    float *cst;      // [Kp]     log w - 1/2 sum_d log sigma^2 (-inf on padding)
+    float *s_kd;     // [Kp][Dp] 1/sigma, dimension-contiguous (statistics)
+    float *mu_kd;    // [Kp][Dp] mu (statistics: t = (x - mu) / sigma)
+    // shared by both forms (finalise)
+    double *alpha;   // [K] 1/sqrt(w)
+    double *beta;    // [K] 1/sqrt(2w)
+    double *mu64;    // [K][D]
+    double *isd64;   // [K][D] 1/sigma
+    double *prec64;  // [K][D] 1/sigma^2
+    // BF16 form: B operands of the log-likelihood GEMM, [term][Kp][D16] bf16,
+    // terms = Q_hi, Q_lo, R_hi, R_lo with Q = mu/sigma^2, R = -1/(2 sigma^2)
+    uint16_t *bimg;
+    float *cfull;    // [Kp] log w - 1/2 sum log sigma^2 - 1/2 sum mu^2/sigma^2 (FP64 -> FP32; -inf on padding)
+};
+
+}  // namespace fv
+
+struct fv_gmm {
+    int K, D;
+    int Kp;     // components padded (64 for FP32, 128 for BF16)
+    int Dp;     // dimensions padded to 8 (FP32 statistics) / 16 (BF16)
+    int prec;   // fv_precision
+    int device;
+    fv::GmmDev dev;
+    void *block;   // single device allocation backing dev.*
+    size_t block_bytes;
+};
+
+namespace fv {
+
+// ---- work description shared by the kernels ---------------------------------
+struct FrameInfo {
+    int64_t row0;    // first row in the packed descriptor array
+    int64_t n;       // descriptors in the frame
+    int32_t slot0;   // first statistics slot of the frame
+    int32_t nslots;  // number of row ranges (slots) of the frame
+};
+
+struct StatUnit {
+    int64_t row0;    // first row of the range
+    int32_t nrows;   // rows in the range
+    int32_t slot;    // statistics slot written by this range
+};
+
+// ---- kernels' host launchers --------------------------------------------------
+cudaError_t launch_prep(const fv_gmm *g, const float *w, const float *mu, const float *var, cudaStream_t st);
+
+cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma,
+                                  cudaStream_t st);
+cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
+                             int n_units, float *part, int P, cudaStream_t st);
+
+// Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,
+// L2. raw_moments selects the BF16 form's [S1, S2hi, S2lo, S0] layout
+// (P = 3D+1) over the FP32 form's centred [U, sum g t^2, S0] (P = 2D+1).
+cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments,
+                            const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st);
+
+}  // namespace fv

@@ -1,0 +1,219 @@
+"""Thin Python binding of the C ABI in include/fv.h (ctypes).
+
+The functions keep the C names and only marshal arguments: pointers, sizes,
+on-device flags and the current CUDA stream of torch. Every step of the
+encoder runs in the CUDA library ``_build/libfvgpu.so``; there is no CPU or
+PyTorch fallback. If the library cannot be built or loaded, importing this
+module raises.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays (host memory).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FV_OK = 0
+FV_PENDING = 1
+FV_ERR_INVALID = -1
+FV_ERR_OOM = -2
+FV_ERR_CUDA = -3
+FV_ERR_BUSY = -4
+FV_ERR_TIMEOUT = -5
+FV_ERR_NOTFOUND = -6
+FV_ERR_EMPTY = -7
+FV_ERR_DEVICE = -8
+FV_ERR_UNSUPPORTED = -9
+
+FV_PREC_FP32 = 0
+FV_PREC_BF16 = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FVError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fv status {status}: {msg}")
+        self.status = status
+
+
+class fv_gmm_desc(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("D", ctypes.c_int), ("weights", ctypes.c_void_p),
+                ("means", ctypes.c_void_p), ("variances", ctypes.c_void_p)]
+
+
+def lib():
+    """Load (building first if needed) the CUDA library. Raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+            P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+            L.fv_gmm_load.argtypes = [ctypes.POINTER(fv_gmm_desc), I, ctypes.POINTER(P)]
+            L.fv_gmm_load.restype = I
+            L.fv_gmm_free.argtypes = [P]
+            L.fv_gmm_free.restype = None
+            L.fv_gmm_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+            L.fv_gmm_info.restype = I
+            L.fv_limits.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I)]
+            L.fv_limits.restype = I
+            L.fv_encode.argtypes = [P, P, I64, I, P, I, P]
+            L.fv_encode.restype = I
+            L.fv_encode_batch.argtypes = [P, P, P, I, I, P, I, P]
+            L.fv_encode_batch.restype = I
+            L.fv_encode_batch_bf16.argtypes = [P, P, I64, P, I, P, P]
+            L.fv_encode_batch_bf16.restype = I
+            L.fv_last_error.argtypes = []
+            L.fv_last_error.restype = ctypes.c_char_p
+            L.fv_prof_enable.argtypes = [I]
+            L.fv_prof_enable.restype = I
+            L.fv_prof_collect.argtypes = [P, I, ctypes.POINTER(I)]
+            L.fv_prof_collect.restype = I
+            L.fv_launch_count.argtypes = []
+            L.fv_launch_count.restype = I64
+            _lib = L
+    return _lib
+
+
+def fv_last_error() -> str:
+    return lib().fv_last_error().decode()
+
+
+def _check(st: int, allow=(FV_OK,)) -> int:
+    if st not in allow:
+        raise FVError(st, fv_last_error())
+    return st
+
+
+def _ptr(a):
+    """(pointer, on_device) of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+class Gmm:
+    """Owns an fv_gmm handle (freed on close/garbage collection)."""
+
+    def __init__(self, handle, K, D, precision):
+        self.handle = handle
+        self.K, self.D, self.precision = K, D, precision
+
+    @property
+    def fv_len(self):
+        return 2 * self.K * self.D
+
+    def close(self):
+        if self.handle:
+            lib().fv_gmm_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fv_gmm_load(weights, means, variances, precision: int = FV_PREC_FP32) -> Gmm:
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+    mu = np.ascontiguousarray(np.asarray(means, dtype=np.float32))
+    var = np.ascontiguousarray(np.asarray(variances, dtype=np.float32))
+    K, D = mu.shape
+    desc = fv_gmm_desc(K, D, w.ctypes.data, mu.ctypes.data, var.ctypes.data)
+    h = ctypes.c_void_p()
+    _check(lib().fv_gmm_load(ctypes.byref(desc), int(precision), ctypes.byref(h)))
+    return Gmm(h, K, D, precision)
+
+
+def fv_gmm_free(g: Gmm) -> None:
+    g.close()
+
+
+def fv_gmm_info(g: Gmm):
+    K, D, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().fv_gmm_info(g.handle, ctypes.byref(K), ctypes.byref(D), ctypes.byref(P)))
+    return K.value, D.value, P.value
+
+
+def fv_limits(precision: int):
+    K, D = ctypes.c_int(), ctypes.c_int()
+    _check(lib().fv_limits(int(precision), ctypes.byref(K), ctypes.byref(D)))
+    return K.value, D.value
+
+
+def fv_encode(g: Gmm, X, out, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    """C fv_encode: X (N x D float32) -> out (2KD float32). Returns the status."""
+    xp, xd = _ptr(X)
+    op, od = _ptr(out)
+    N = int(X.shape[0])
+    return _check(lib().fv_encode(g.handle, xp, N, xd, op, od, _stream(stream)), allow)
+
+
+def fv_encode_batch(g: Gmm, X_packed, offsets, out, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    """C fv_encode_batch: offsets is a host int64 array of B+1 entries."""
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    B = offs.size - 1
+    xp, xd = _ptr(X_packed)
+    op, od = _ptr(out)
+    return _check(lib().fv_encode_batch(g.handle, xp, offs.ctypes.data, B, xd, op, od, _stream(stream)), allow)
+
+
+def fv_encode_batch_bf16(g: Gmm, X_bf16, ld_x: int, offsets, out, stream=None,
+                         allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    """C fv_encode_batch_bf16: X_bf16 is a CUDA tensor of bfloat16 (or int16
+    bit patterns) with row pitch ld_x; out a CUDA float32 tensor."""
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    B = offs.size - 1
+    xp, _ = _ptr(X_bf16)
+    op, _ = _ptr(out)
+    return _check(lib().fv_encode_batch_bf16(g.handle, xp, int(ld_x), offs.ctypes.data, B, op, _stream(stream)),
+                  allow)
+
+
+class fv_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+def fv_prof_enable(on: bool) -> None:
+    _check(lib().fv_prof_enable(int(bool(on))))
+
+
+def fv_prof_collect() -> dict:
+    """{kernel name: (launches, total device ms)} since the last collect."""
+    arr = (fv_kernel_stat * 64)()
+    n = ctypes.c_int()
+    _check(lib().fv_prof_collect(ctypes.cast(arr, ctypes.c_void_p), 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def fv_launch_count() -> int:
+    return int(lib().fv_launch_count())
