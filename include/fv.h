@@ -134,6 +134,28 @@ FV_API int fv_encode_batch(const fv_gmm *gmm, const float *X_packed, const int64
 FV_API int fv_encode_batch_bf16(const fv_gmm *gmm, const uint16_t *X_bf16, int64_t ld_x,
                          const int64_t *offsets, int B, float *fv_out, void *cuda_stream);
 
+/* Allocation-free variant of fv_encode (plain FP32 form, one descriptor set).
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory, e.g. an application whose own allocator already
+ * owns nearly all of it, a latency-critical loop that cannot risk a memory
+ * pool growing, or a process under a fixed memory quota. Instead of taking
+ * scratch from the memory pool, it uses one fixed 32 MiB __device__ array
+ * inside the library (held on every GPU that loads the library until the
+ * process exits) and calls no allocating routine.
+ *   gmm      an FV_PREC_FP32 handle on the current device,
+ *   X        N x D float32 row-major descriptors, DEVICE memory,
+ *   fv_out   2*K*D float32, DEVICE memory.
+ * The scratch needs about N*Kp*4 bytes for the posteriors (Kp = K rounded up
+ * to 64) plus the per-range statistics; larger inputs are rejected with
+ * FV_ERR_UNSUPPORTED and a message giving the limit (e.g. N=19200, K=256,
+ * D=64 fits). The first call on a device looks up the array's device address
+ * (make that first call before any stream capture). All calls share the
+ * array and it keeps the last call's contents; calls whose GPU work overlaps
+ * (other streams, other threads) race on it, so serialise them. Returns after
+ * queuing the work on cuda_stream. Errors: FV_ERR_INVALID, FV_ERR_UNSUPPORTED,
+ * FV_ERR_EMPTY (N == 0; zero vector), FV_ERR_CUDA. */
+FV_API int fv_encode_noalloc(const fv_gmm *gmm, const float *X, int64_t N, float *fv_out, void *cuda_stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 FV_API const char *fv_last_error(void);
 

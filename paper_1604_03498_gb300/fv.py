@@ -72,6 +72,8 @@ def lib():
             L.fv_encode_batch_bf16.restype = I
             L.fv_last_error.argtypes = []
             L.fv_last_error.restype = ctypes.c_char_p
+            L.fv_encode_noalloc.argtypes = [P, P, I64, P, P]
+            L.fv_encode_noalloc.restype = I
             L.fv_prof_enable.argtypes = [I]
             L.fv_prof_enable.restype = I
             L.fv_prof_collect.argtypes = [P, I, ctypes.POINTER(I)]
@@ -197,6 +199,15 @@ def fv_encode_batch_bf16(g: Gmm, X_bf16, ld_x: int, offsets, out, stream=None,
     op, _ = _ptr(out)
     return _check(lib().fv_encode_batch_bf16(g.handle, xp, int(ld_x), offs.ctypes.data, B, op, _stream(stream)),
                   allow)
+
+
+def fv_encode_noalloc(g: Gmm, X, out, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    """C fv_encode_noalloc: like fv_encode (FP32 handle, device tensors only)
+    but for callers that must not allocate device memory: the library takes
+    its scratch from a fixed array it owns instead of the memory pool."""
+    xp, _ = _ptr(X)
+    op, _ = _ptr(out)
+    return _check(lib().fv_encode_noalloc(g.handle, xp, int(X.shape[0]), op, _stream(stream)), allow)
 
 
 class fv_kernel_stat(ctypes.Structure):
