@@ -83,6 +83,7 @@ struct Stage {
     }
 };
 thread_local Stage t_stage;
+thread_local uint32_t t_err_word = 0;   // device error word copied back by host-output calls
 
 // Copy `bytes` from host `src` to device `dst` on `st` through a pinned slot.
 cudaError_t stage_upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
@@ -209,11 +210,14 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     const size_t o_fr = s.take(sizeof(FrameInfo) * B);
     const size_t o_un = s.take(sizeof(StatUnit) * std::max(nslots, 1));
     const size_t o_sq = s.take(sizeof(double) * (size_t)B * K);
+    const size_t o_err = s.take(sizeof(uint32_t));
     const size_t o_out = !out_on_device ? s.take(sizeof(float) * fvlen * B) : 0;
     cudaError_t e = cudaMallocAsync((void **)&s.base, s.off, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
 
     int rc = FV_OK;
+    bool check_err_word = false;
+    t_err_word = 0;
     do {
         const void *Xd = X;
         if (need_x_f32_stage) {
@@ -234,6 +238,11 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
         }
         float *part = (float *)(s.base + o_part);
         double *sq = (double *)(s.base + o_sq);
+        uint32_t *errd = (uint32_t *)(s.base + o_err);
+        if ((e = cudaMemsetAsync(errd, 0, sizeof(uint32_t), st)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemsetAsync(error word)");
+            break;
+        }
         if (!bf16) {
             float *gam = (float *)(s.base + o_gam);
             if ((e = launch_f32_posteriors(g, (const float *)Xd, rows, gam, st)) != cudaSuccess) {
@@ -255,19 +264,22 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
                 xb = xconv;
             }
             uint16_t *gam = (uint16_t *)(s.base + o_gam);
-            rc = run_bf16_encoder(g, xb, ldx_dev, rows, gam, und, nslots, part, P, sms, st);
+            rc = run_bf16_encoder(g, xb, ldx_dev, rows, gam, und, nslots, part, P, sms, errd, st);
             if (rc != FV_OK) break;
         }
-        if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st)) != cudaSuccess) {
+        if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd)) != cudaSuccess) {
             rc = cuda_fail(e, "finalise launch");
             break;
         }
         if (!out_on_device) {
             if ((e = cudaMemcpyAsync(fv_out, outd, sizeof(float) * fvlen * B, cudaMemcpyDeviceToHost, st)) !=
-                cudaSuccess) {
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(&t_err_word, errd, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) !=
+                    cudaSuccess) {
                 rc = cuda_fail(e, "cudaMemcpyAsync(fv_out)");
                 break;
             }
+            check_err_word = true;
         }
     } while (0);
     cudaError_t ef = cudaFreeAsync(s.base, st);
@@ -275,6 +287,9 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     if (rc == FV_OK && !out_on_device) {
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
     }
+    if (rc == FV_OK && check_err_word && t_err_word != 0)
+        rc = fail(FV_ERR_DEVICE, "a kernel gave up on a bounded wait (error word " + std::to_string(t_err_word) +
+                                     "); the output is NaN");
     if (rc == FV_OK && plan.nonempty == 0) rc = fail(FV_ERR_EMPTY, "no descriptors (N == 0)");
     return rc;
 }

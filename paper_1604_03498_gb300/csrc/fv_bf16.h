@@ -12,7 +12,9 @@ int64_t bf16_rows_per_range(const fv_gmm *g, int64_t rows, int sms);
 cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, uint16_t *Xb, cudaStream_t st);
 
 // Posteriors and statistics of the BF16 form; returns an fv_status.
+// err: device word a kernel sets when a bounded wait gives up (zeroed by the caller).
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
-                     const StatUnit *units, int n_units, float *part, int P, int sms, cudaStream_t st);
+                     const StatUnit *units, int n_units, float *part, int P, int sms, uint32_t *err,
+                     cudaStream_t st);
 
 }  // namespace fv

@@ -9,7 +9,8 @@
 // squares. Kernel B: one block per frame, sums the K squares in a fixed tree
 // order and scales the frame's vector by 1/||z||.
 //
-// FP32 form slots hold [U (D), W = sum g t^2 (D), S0]: v = (W - S0) beta / N.
+// FP32 form slots hold centred sums [A = sum g (x-mu) (D), B = sum g (x-mu)^2
+// (D), S0]: u = A/sigma alpha/N, v = (B/sigma^2 - S0) beta/N.
 // BF16 form slots hold raw moments [S1 (D), S2hi (D), S2lo (D), S0] and the
 // centring happens here in FP64:
 //   u = (S1 - mu S0) / sigma * alpha / N
@@ -43,11 +44,21 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
         if (threadIdx.x == 0) sq[(size_t)f * K + k] = 0.0;
         return;
     }
+    const size_t sstride = (size_t)Kp * P;
     for (int j = threadIdx.x; j < P; j += FA_THREADS) {
-        double a = 0.0;
+        // four interleaved partial sums keep four loads in flight; the
+        // combination order is fixed
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         const float *p = part + ((size_t)fr.slot0 * Kp + k) * P + j;
-        for (int s = 0; s < fr.nslots; ++s) a += (double)p[(size_t)s * Kp * P];
-        sacc[j] = a;
+        int s = 0;
+        for (; s + 4 <= fr.nslots; s += 4) {
+            a0 += (double)p[(size_t)s * sstride];
+            a1 += (double)p[(size_t)(s + 1) * sstride];
+            a2 += (double)p[(size_t)(s + 2) * sstride];
+            a3 += (double)p[(size_t)(s + 3) * sstride];
+        }
+        for (; s < fr.nslots; ++s) a0 += (double)p[(size_t)s * sstride];
+        sacc[j] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     const double S0 = sacc[P - 1];
@@ -63,8 +74,8 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
             u = (S1 - m * S0) * g.isd64[(size_t)k * D + d] * al;
             v = ((S2 - 2.0 * m * S1 + m * m * S0) * g.prec64[(size_t)k * D + d] - S0) * be;
         } else {
-            u = sacc[d] * al;
-            v = (sacc[D + d] - S0) * be;
+            u = sacc[d] * g.isd64[(size_t)k * D + d] * al;
+            v = (sacc[D + d] * g.prec64[(size_t)k * D + d] - S0) * be;
         }
         const double zu = ssqrt(u), zv = ssqrt(v);
         o[(size_t)k * D + d] = (float)zu;
@@ -81,7 +92,8 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
 }
 
 __global__ void __launch_bounds__(FB_THREADS)
-finalize_b_kernel(int K, int D, const double *__restrict__ sq, float *__restrict__ out) {
+finalize_b_kernel(int K, int D, const double *__restrict__ sq, float *__restrict__ out,
+                  const uint32_t *__restrict__ err) {
     __shared__ double red[FB_THREADS];
     const int f = blockIdx.x;
     double a = 0.0;
@@ -93,17 +105,21 @@ finalize_b_kernel(int K, int D, const double *__restrict__ sq, float *__restrict
         __syncthreads();
     }
     const double tot = red[0];
-    if (!(tot > 0.0)) return;   // all-zero vector stays zero
-    const float inv = (float)(1.0 / sqrt(tot));
     const size_t n = (size_t)2 * K * D;
     float *o = out + (size_t)f * n;
+    if (err && *err) {   // an earlier kernel of this call gave up: poison the output
+        for (size_t j = threadIdx.x; j < n; j += FB_THREADS) o[j] = __int_as_float(0x7fc00000);
+        return;
+    }
+    if (!(tot > 0.0)) return;   // all-zero vector stays zero
+    const float inv = (float)(1.0 / sqrt(tot));
     for (size_t j = threadIdx.x; j < n; j += FB_THREADS) o[j] *= inv;
 }
 
 }  // namespace
 
 cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments, const FrameInfo *frames,
-                            int B, double *sq, float *out, cudaStream_t st) {
+                            int B, double *sq, float *out, cudaStream_t st, const uint32_t *err) {
     if (B <= 0) return cudaSuccess;
     dim3 grid_a((unsigned)g->K, (unsigned)B);
     const size_t smem = sizeof(double) * P;
@@ -126,7 +142,7 @@ cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_
     if (e != cudaSuccess) return e;
     {
         KernelTimer kt_("finalize_b", st);
-        finalize_b_kernel<<<(unsigned)B, FB_THREADS, 0, st>>>(g->K, g->D, sq, out);
+        finalize_b_kernel<<<(unsigned)B, FB_THREADS, 0, st>>>(g->K, g->D, sq, out, err);
     }
     return cudaGetLastError();
 }

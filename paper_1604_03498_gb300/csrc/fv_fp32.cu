@@ -10,9 +10,10 @@
 // Statistics (Algorithm 1 second loop; the paper's Phase 2, Algorithm 3 with
 // one private copy of U, V per block): each block owns one row range and one
 // 64-component chunk and accumulates, per (k, d) held in registers,
-//   U_kd += gamma_ik t_ikd,  W_kd += gamma_ik t_ikd^2,  S0_k += gamma_ik
-// (V = W - S0 is formed by the finalise kernel). Here t is formed as
-// (x - mu) * (1/sigma), whose rounding error is relative to t itself; the
+//   A_kd += gamma_ik (x_id - mu_kd),  B_kd += gamma_ik (x_id - mu_kd)^2,
+//   S0_k += gamma_ik
+// and the finalise kernel forms U = A/sigma and V = B/sigma^2 - S0 in FP64.
+// The residual x - mu carries a rounding error relative to itself; the
 // posteriors' single-FMA form x/sigma - mu/sigma errs by ~eps |mu/sigma|, which
 // is harmless inside a softmax but would be amplified near zero by the signed
 // square root when a component's variance is tiny. Every block writes its own
@@ -136,14 +137,18 @@ constexpr int S_CPT = 4;   // components per thread
 constexpr int S_DPT = 8;   // dimensions per thread
 constexpr int S_THREADS = (S_KC / S_CPT) * (S_DC / S_DPT);  // 128
 
+constexpr int S_PER_THREAD = S_RS * S_KC / S_THREADS;  // 16 staged values of each kind per thread
+
 // grid.x = statistics units (row ranges), grid.y = 64-component chunks,
-// grid.z = 64-dimension chunks.
-__global__ void __launch_bounds__(S_THREADS)
-f32_stats_kernel(const float *__restrict__ X, int D, int Dp, const float *__restrict__ gamma, int Kp,
-                 const float *__restrict__ s_kd, const float *__restrict__ mu_kd,
-                 const StatUnit *__restrict__ units, float *__restrict__ part, int P) {
-    __shared__ __align__(16) float sG[S_RS * S_KC];
-    __shared__ __align__(16) float sXs[S_RS * S_DC];
+// grid.z = 64-dimension chunks. Stages of 32 rows are double-buffered: the
+// next stage's posteriors and descriptors are loaded into registers while the
+// current one is consumed from shared memory.
+__global__ void __launch_bounds__(S_THREADS, 3)
+f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ gamma, int Kp, int Dp,
+                 const float *__restrict__ mu_kd, const StatUnit *__restrict__ units, float *__restrict__ part,
+                 int P) {
+    __shared__ __align__(16) float sG[2][S_RS * S_KC];
+    __shared__ __align__(16) float sXs[2][S_RS * S_DC];
 
     const StatUnit u = units[blockIdx.x];
     const int kc0 = blockIdx.y * S_KC, dc0 = blockIdx.z * S_DC;
@@ -152,36 +157,53 @@ f32_stats_kernel(const float *__restrict__ X, int D, int Dp, const float *__rest
     const int kb = kc0 + cg * S_CPT, dl = dg * S_DPT, db = dc0 + dl;
     const bool active = db < D;
 
-    float s[S_CPT][S_DPT], n[S_CPT][S_DPT], U[S_CPT][S_DPT], W[S_CPT][S_DPT], S0[S_CPT];
+    float m[S_CPT][S_DPT], U[S_CPT][S_DPT], W[S_CPT][S_DPT], S0[S_CPT];
 #pragma unroll
     for (int c = 0; c < S_CPT; ++c) {
         S0[c] = 0.f;
 #pragma unroll
         for (int j = 0; j < S_DPT; ++j) {
-            s[c][j] = active ? s_kd[(size_t)(kb + c) * Dp + db + j] : 0.f;
-            n[c][j] = active ? mu_kd[(size_t)(kb + c) * Dp + db + j] : 0.f;
+            m[c][j] = active ? mu_kd[(size_t)(kb + c) * Dp + db + j] : 0.f;
             U[c][j] = 0.f;
             W[c][j] = 0.f;
         }
     }
 
+    float rg[S_PER_THREAD], rx[S_PER_THREAD];
+    auto load = [&](int r0) {
+#pragma unroll
+        for (int q = 0; q < S_PER_THREAD; ++q) {
+            const int i = tid + q * S_THREADS;
+            const int r = i / S_KC, kk = i % S_KC, d = dc0 + kk;
+            const bool rok = r0 + r < u.nrows;
+            const int64_t row = u.row0 + r0 + r;
+            rg[q] = rok ? gamma[row * Kp + kc0 + kk] : 0.f;
+            rx[q] = (rok && d < D) ? X[row * D + d] : 0.f;
+        }
+    };
+    auto store = [&](int b) {
+#pragma unroll
+        for (int q = 0; q < S_PER_THREAD; ++q) {
+            sG[b][tid + q * S_THREADS] = rg[q];
+            sXs[b][tid + q * S_THREADS] = rx[q];
+        }
+    };
+
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
     for (int r0 = 0; r0 < u.nrows; r0 += S_RS) {
-        const int nr = min(S_RS, u.nrows - r0);
-        __syncthreads();
-        for (int i = tid; i < S_RS * S_KC; i += S_THREADS) {
-            const int r = i / S_KC, kk = i % S_KC;
-            sG[i] = r < nr ? gamma[(u.row0 + r0 + r) * Kp + kc0 + kk] : 0.f;
-        }
-        for (int i = tid; i < S_RS * S_DC; i += S_THREADS) {
-            const int r = i / S_DC, dd = i % S_DC, d = dc0 + dd;
-            sXs[i] = (r < nr && d < D) ? X[(u.row0 + r0 + r) * D + d] : 0.f;
-        }
-        __syncthreads();
+        const bool more = r0 + S_RS < u.nrows;
+        if (more) load(r0 + S_RS);
         if (active) {
-            for (int r = 0; r < nr; ++r) {
-                const float4 g4 = *reinterpret_cast<const float4 *>(&sG[r * S_KC + cg * S_CPT]);
-                const float4 xa = *reinterpret_cast<const float4 *>(&sXs[r * S_DC + dl]);
-                const float4 xb = *reinterpret_cast<const float4 *>(&sXs[r * S_DC + dl + 4]);
+            const float *G = sG[buf];
+            const float *Xs = sXs[buf];
+#pragma unroll 4
+            for (int r = 0; r < S_RS; ++r) {
+                const float4 g4 = *reinterpret_cast<const float4 *>(&G[r * S_KC + cg * S_CPT]);
+                const float4 xa = *reinterpret_cast<const float4 *>(&Xs[r * S_DC + dl]);
+                const float4 xb = *reinterpret_cast<const float4 *>(&Xs[r * S_DC + dl + 4]);
                 const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
                 const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
@@ -189,14 +211,17 @@ f32_stats_kernel(const float *__restrict__ X, int D, int Dp, const float *__rest
                     S0[c] += gv[c];
 #pragma unroll
                     for (int j = 0; j < S_DPT; ++j) {
-                        const float t = (xv[j] - n[c][j]) * s[c][j];
-                        const float gt = gv[c] * t;
-                        U[c][j] += gt;
-                        W[c][j] = fmaf(gt, t, W[c][j]);
+                        const float dx = xv[j] - m[c][j];
+                        const float gd = gv[c] * dx;
+                        U[c][j] += gd;
+                        W[c][j] = fmaf(gd, dx, W[c][j]);
                     }
                 }
             }
         }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
     }
     if (!active) return;
     float *dst = part + (size_t)u.slot * Kp * P;
@@ -250,8 +275,7 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
     dim3 grid((unsigned)n_units, (unsigned)(g->Kp / S_KC), (unsigned)((g->D + S_DC - 1) / S_DC));
     {
         KernelTimer kt_("f32_stats", st);
-        f32_stats_kernel<<<grid, S_THREADS, 0, st>>>(X, g->D, g->Dp, gamma, g->Kp, g->dev.s_kd, g->dev.mu_kd, units,
-                                                 part, P);
+        f32_stats_kernel<<<grid, S_THREADS, 0, st>>>(X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units, part, P);
     }
     return cudaGetLastError();
 }

@@ -106,7 +106,10 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 // Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,
 // L2. raw_moments selects the BF16 form's [S1, S2hi, S2lo, S0] layout
 // (P = 3D+1) over the FP32 form's centred [U, sum g t^2, S0] (P = 2D+1).
+// err (nullable): device error word of the call; when a kernel set it, every
+// output element becomes NaN so a failed encode can never look valid.
 cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments,
-                            const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st);
+                            const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
+                            const uint32_t *err = nullptr);
 
 }  // namespace fv
