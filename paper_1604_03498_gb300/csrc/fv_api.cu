@@ -209,7 +209,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     const size_t o_part = s.take(sizeof(float) * std::max(nslots, 1) * (size_t)Kp * P);
     const size_t o_fr = s.take(sizeof(FrameInfo) * B);
     const size_t o_un = s.take(sizeof(StatUnit) * std::max(nslots, 1));
-    const size_t o_sq = s.take(sizeof(double) * (size_t)B * K);
+    const size_t o_sq = s.take(sizeof(double) * (size_t)B * (Kp / 32) * ((D + 7) / 8));
     const size_t o_err = s.take(sizeof(uint32_t));
     const size_t o_out = !out_on_device ? s.take(sizeof(float) * fvlen * B) : 0;
     cudaError_t e = cudaMallocAsync((void **)&s.base, s.off, st);

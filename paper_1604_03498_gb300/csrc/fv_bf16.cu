@@ -45,7 +45,8 @@ using namespace sm100;
 
 namespace {
 
-constexpr int kThreads = 256;          // 8 warps
+constexpr int kThreads = 256;          // statistics kernel: 8 warps
+constexpr int kPostThreads = 384;      // posteriors kernel: 12 warps
 constexpr int kTileRows = 128;         // posteriors tile (MMA M)
 constexpr int kStatRows = 64;          // statistics stage rows
 constexpr int kStatStages = 3;
@@ -85,14 +86,14 @@ struct PostArgs {
     int split;      // CTAs per cluster sharing a row tile (1 or 2)
     int nstage;     // A-operand stages (1 or 2)
     uint32_t tmem_cols;
-    const float *cfull;   // [Kp] log-constant (-inf on padding)
+    const float *cl2;     // [Kp] log-constant times log2(e) (-inf on padding)
     uint16_t *gamma;      // [rows][Kp] bf16 posteriors
     uint32_t *err;
 };
 
 struct PostSmem {
     // byte offsets from the (1024-aligned) dynamic shared-memory base
-    uint32_t b, a, c, xchg, bars, misc, total;
+    uint32_t b, a, hx, xchg, bars, misc, total;
     uint32_t a_stage;   // bytes per A stage
 };
 
@@ -104,13 +105,13 @@ __host__ __device__ inline PostSmem post_smem(int nkb, int ncta, int nstage, int
     s.a_stage = 3u * nkb * kTileRows * 32u;
     s.a = off;
     off += nstage * s.a_stage;
-    s.c = off;
-    off += ncta * 4u;
+    s.hx = off;                       // (max, sum) of each row's two column halves
+    off += 2u * kTileRows * 8u;
     s.xchg = off;
     off += split > 1 ? 2u * kTileRows * 8u : 0u;
     off = (off + 15u) & ~15u;
     s.bars = off;
-    off += 16u * 8u;
+    off += 24u * 8u;
     s.misc = off;
     off += 16u;
     s.total = off;
@@ -119,9 +120,9 @@ __host__ __device__ inline PostSmem post_smem(int nkb, int ncta, int nstage, int
 
 // Barrier indices in the barrier array.
 enum { PB_BFULL = 0, PB_XFULL = 1, PB_AFULL = 3, PB_AEMPTY = 5, PB_LFULL = 7, PB_LEMPTY = 9, PB_XCHG = 11,
-       PB_DRAIN = 13 };
+       PB_DRAIN = 13, PB_HXFULL = 16, PB_HXFREE = 20 };
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kPostThreads, 1)
 bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB,
                        PostArgs p) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -130,7 +131,6 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);   // [0] tmem base, [1] abort
     volatile uint32_t *abort_flag = misc + 1;
-    float *sC = reinterpret_cast<float *>(smem + L.c);
 
     if ((smem_u32(smem) & 1023u) != 0u) {   // layout assumption broken: refuse to run
         if (threadIdx.x == 0) atomicOr(p.err, kErrAlign);
@@ -146,15 +146,17 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
             mbar_init(&bars[PB_AFULL + s], 2);
             mbar_init(&bars[PB_AEMPTY + s], 1);
             mbar_init(&bars[PB_LFULL + s], 1);
-            mbar_init(&bars[PB_LEMPTY + s], 4);
+            mbar_init(&bars[PB_LEMPTY + s], 8);
             mbar_init(&bars[PB_XCHG + s], kTileRows);
         }
         mbar_init(&bars[PB_DRAIN], 1);
+        for (int q = 0; q < 4; ++q) {
+            mbar_init(&bars[PB_HXFULL + q], 64);
+            mbar_init(&bars[PB_HXFREE + q], 64);
+        }
         misc[1] = 0u;
         fence_mbar_init();
     }
-    // per-CTA log-constants in log2 units
-    for (int k = threadIdx.x; k < p.ncta; k += kThreads) sC[k] = p.cfull[rank * p.ncta + k] * kLog2e;
     if (warp == 1) {
         tmem_alloc(&misc[0], p.tmem_cols);
         tmem_relinquish();
@@ -259,12 +261,21 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
             if (lane == 0) mbar_arrive(&bars[PB_AFULL + s]);
         }
     } else if (warp >= 4) {
-        // ---------------- softmax epilogue: one thread per row ----------------
-        const int q = warp & 3;
+        // ---------------- softmax epilogue ----------------
+        // Two warps per TMEM lane quadrant: warp 4+q and 8+q own rows
+        // 32q..32q+31, each over half of the CTA's columns. Pass A reads L,
+        // forms y = l log2(e) + c log2(e), keeps an online row max/sum with a
+        // reference max per 32-column chunk and stores 2^(y - ref) back into
+        // TMEM; the halves (and, with a component split, the peer CTA) combine
+        // their (max, sum); pass B rescales each chunk and writes bf16.
+        const int q = warp & 3, h = (warp - 4) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        const int nch = p.ncta / 32;
+        const int nh = p.ncta / 64;          // 32-column chunks per half (2, 3 or 4)
+        const int c0 = h * nh;
+        float2 *hx = reinterpret_cast<float2 *>(smem + L.hx);
         float2 *xbuf = reinterpret_cast<float2 *>(smem + L.xchg);
+        const float *cl = p.cl2 + rank * p.ncta;
         int i = 0;
         for (int tile = cluster_id; tile < p.ntiles; tile += nclusters, ++i) {
             const int b = i & 1;
@@ -272,52 +283,83 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
             tc_fence_after();
             const uint32_t ta = lane_base + (uint32_t)(b * p.ncta);
             float v[32];
-            // pass 1: row maximum of y = l*log2(e) (constant folded in)
-            float m = -INFINITY;
-            for (int c = 0; c < nch; ++c) {
-                tmem_ld32(ta + c * 32, v);
+            float m = -INFINITY, z = 0.f;
+            float mc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int k = 0; k < 32; ++k) m = fmaxf(m, fmaf(v[k], kLog2e, sC[c * 32 + k]));
-            }
-            // pass 2: e = 2^(y - m), stored back into TMEM, and their sum
-            float z = 0.f;
-            for (int c = 0; c < nch; ++c) {
+            for (int cc = 0; cc < 4; ++cc) {
+                if (cc >= nh) break;
+                const int c = c0 + cc;
                 tmem_ld32(ta + c * 32, v);
+                const float4 *c4 = reinterpret_cast<const float4 *>(cl + c * 32);
+                float cm = -INFINITY;
+#pragma unroll
+                for (int k4 = 0; k4 < 8; ++k4) {
+                    const float4 cv = __ldg(c4 + k4);
+                    v[4 * k4 + 0] = fmaf(v[4 * k4 + 0], kLog2e, cv.x);
+                    v[4 * k4 + 1] = fmaf(v[4 * k4 + 1], kLog2e, cv.y);
+                    v[4 * k4 + 2] = fmaf(v[4 * k4 + 2], kLog2e, cv.z);
+                    v[4 * k4 + 3] = fmaf(v[4 * k4 + 3], kLog2e, cv.w);
+                    cm = fmaxf(cm, fmaxf(fmaxf(v[4 * k4 + 0], v[4 * k4 + 1]), fmaxf(v[4 * k4 + 2], v[4 * k4 + 3])));
+                }
+                const float mn = fmaxf(m, cm);
+                const float mref = (mn == -INFINITY) ? 0.f : mn;
+                z *= ex2_approx(m - mref);
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
-                    const float e = ex2_approx(fmaf(v[k], kLog2e, sC[c * 32 + k]) - m);
+                    const float e = ex2_approx(v[k] - mref);
                     v[k] = e;
                     z += e;
                 }
                 tmem_st32(ta + c * 32, v);
+                mc[cc] = mref;
+                m = mn;
             }
-            float scale;
+            // combine the two column halves of the row (bounded handshakes:
+            // the partner warp has read the previous tile's value before this
+            // one is written, and has written this tile's before it is read)
+            if (i > 0 && !__all_sync(0xffffffffu, mbar_wait(&bars[PB_HXFREE + q], (i - 1) & 1, abort_flag, p.err)))
+                break;
+            hx[h * kTileRows + r] = make_float2(m, z);
+            mbar_arrive(&bars[PB_HXFULL + q]);
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[PB_HXFULL + q], i & 1, abort_flag, p.err))) break;
+            const float2 o = hx[(h ^ 1) * kTileRows + r];
+            mbar_arrive(&bars[PB_HXFREE + q]);
+            float M = fmaxf(m, o.x);
+            float Mref = (M == -INFINITY) ? 0.f : M;
+            float Z = z * ex2_approx(m - Mref) + o.y * ex2_approx(o.x - Mref);
             if (p.split > 1) {
                 const uint32_t peer = rank ^ 1u;
-                st_cluster_f32x2(mapa(smem_u32(&xbuf[b * kTileRows + r]), peer), m, z);
-                mbar_arrive_remote(mapa(smem_u32(&bars[PB_XCHG + b]), peer));
+                if (h == 0) {
+                    st_cluster_f32x2(mapa(smem_u32(&xbuf[b * kTileRows + r]), peer), M, Z);
+                    mbar_arrive_remote(mapa(smem_u32(&bars[PB_XCHG + b]), peer));
+                }
                 if (!__all_sync(0xffffffffu, mbar_wait(&bars[PB_XCHG + b], (i >> 1) & 1, abort_flag, p.err, true)))
                     break;
-                const float2 o = xbuf[b * kTileRows + r];
-                const float M = fmaxf(m, o.x);
-                const float Z = z * ex2_approx(m - M) + o.y * ex2_approx(o.x - M);
-                scale = ex2_approx(m - M) / Z;
-            } else {
-                scale = 1.0f / z;
+                const float2 po = xbuf[b * kTileRows + r];
+                const float M2 = fmaxf(M, po.x);
+                const float M2ref = (M2 == -INFINITY) ? 0.f : M2;
+                Z = Z * ex2_approx(M - M2ref) + po.y * ex2_approx(po.x - M2ref);
+                M = M2;
+                Mref = M2ref;
             }
-            // pass 3: normalised posteriors -> bf16 global
+            const float inv = 1.0f / Z;
+            // pass B: normalised posteriors -> bf16 global
             const int64_t row = (int64_t)tile * kTileRows + r;
             uint16_t *g = p.gamma + row * p.Kp + rank * p.ncta;
-            for (int c = 0; c < nch; ++c) {
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                if (cc >= nh) break;
+                const int c = c0 + cc;
                 tmem_ld32(ta + c * 32, v);
+                const float sc = ex2_approx(mc[cc] - Mref) * inv;
                 if (row < p.rows) {
                     uint4 *dst = reinterpret_cast<uint4 *>(g + c * 32);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        dst[k] = make_uint4(pack_bf16x2(v[8 * k + 0] * scale, v[8 * k + 1] * scale),
-                                            pack_bf16x2(v[8 * k + 2] * scale, v[8 * k + 3] * scale),
-                                            pack_bf16x2(v[8 * k + 4] * scale, v[8 * k + 5] * scale),
-                                            pack_bf16x2(v[8 * k + 6] * scale, v[8 * k + 7] * scale));
+                        dst[k] = make_uint4(pack_bf16x2(v[8 * k + 0] * sc, v[8 * k + 1] * sc),
+                                            pack_bf16x2(v[8 * k + 2] * sc, v[8 * k + 3] * sc),
+                                            pack_bf16x2(v[8 * k + 4] * sc, v[8 * k + 5] * sc),
+                                            pack_bf16x2(v[8 * k + 6] * sc, v[8 * k + 7] * sc));
                 }
             }
             tc_fence_before();
@@ -488,7 +530,7 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
             const int D16 = p.nkb * 16;
             for (int c = 0; c < nchunk; ++c) {
                 const int k = kc0 + c * 128 + q * 32 + lane;
-                float *dst = p.part + ((size_t)u.slot * p.Kp + k) * p.P;
+                float *dst = p.part + (size_t)u.slot * p.Kp * p.P + k;   // part[slot][j][Kp]
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * p.ny);
                 for (int n0 = 0; n0 < p.ny; n0 += 32) {
                     float v[32];
@@ -499,9 +541,9 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
                         if (n >= p.ny) continue;
                         const int part = n / D16, d = n - part * D16;
                         if (part < 3) {
-                            if (d < p.D) dst[part * p.D + d] = v[e];
+                            if (d < p.D) dst[(size_t)(part * p.D + d) * p.Kp] = v[e];
                         } else if (d == 0) {
-                            dst[3 * p.D] = v[e];
+                            dst[(size_t)(3 * p.D) * p.Kp] = v[e];
                         }
                     }
                 }
@@ -579,18 +621,19 @@ bool bf16_config(const fv_gmm *g, BfCfg &c) {
     c.sc = (g->Kp % 256 == 0) ? 256 : 128;
     c.ny = 3 * nkb * 16 + 16;
     c.stat_smem = stat_smem(nkb, c.sc).total;
-    return c.post_smem <= (size_t)maxsmem && c.stat_smem <= (size_t)maxsmem && c.ncta % 16 == 0 && c.ncta <= 256 &&
+    return c.post_smem <= (size_t)maxsmem && c.stat_smem <= (size_t)maxsmem && c.ncta % 64 == 0 && c.ncta <= 256 &&
            c.ny <= 256;
 }
 
 }  // namespace
 
 int64_t bf16_rows_per_range(const fv_gmm *g, int64_t rows, int sms) {
-    // about one statistics CTA per SM, ranges of at least 256 rows (a slot is
-    // K x (3D+1) floats, so shorter ranges cost more slot traffic than rows)
+    // about two waves of equal statistics CTAs (one CTA per SM), ranges of at
+    // least 256 rows (a slot is K x (3D+1) floats, so shorter ranges would cost
+    // more slot traffic than posterior reads)
     const int sc = (g->Kp % 256 == 0) ? 256 : 128;
     const int64_t per_range = g->Kp / sc;
-    int64_t rpr = (rows * per_range + sms - 1) / std::max(1, sms);
+    int64_t rpr = (rows * per_range + 2LL * sms - 1) / std::max(1, 2 * sms);
     rpr = round_up64(std::max<int64_t>(rpr, 256), kStatRows);
     return std::min<int64_t>(rpr, 16384);
 }
@@ -633,7 +676,7 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     pa.split = c.split;
     pa.nstage = c.nstage;
     pa.tmem_cols = pow2_cols(2 * c.ncta);
-    pa.cfull = g->dev.cfull;
+    pa.cl2 = g->dev.cl2;
     pa.gamma = gamma;
     pa.err = err;
     cudaError_t e = cudaFuncSetAttribute(bf16_posteriors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -643,7 +686,7 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)(nclusters * c.split));
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kPostThreads);
     cfg.dynamicSmemBytes = c.post_smem;
     cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;

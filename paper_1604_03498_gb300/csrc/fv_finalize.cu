@@ -1,110 +1,125 @@
 // Finalise: reduction of the per-range statistics copies (the paper's second
-// Phase-2 kernel, Algorithm 3: "each block processes U and V for one GMM
-// component" and adds the per-block copies) followed by the encoding scheme of
-// Sec. 4: u = U/(N sqrt(w)), v = V/(N sqrt(2w)), signed square root, L2.
+// Phase-2 kernel, Algorithm 3, adding the per-block copies of U and V)
+// followed by the encoding scheme of Sec. 4: u = U/(N sqrt(w)),
+// v = V/(N sqrt(2w)), signed square root, L2.
 //
-// Kernel A: one block per (component, frame). Sums that frame's slots in slot
-// order (fixed, so a frame's vector does not depend on what else ran with it),
-// forms u and v in FP64, writes sign(z) sqrt|z| and the component's sum of
-// squares. Kernel B: one block per frame, sums the K squares in a fixed tree
-// order and scales the frame's vector by 1/||z||.
+// Slots are component-fastest: part[slot][j][Kp], j indexing the statistic.
+// Kernel A: one block per (32 components x 8 dimensions, frame); each thread
+// sums the frame's slots for its (component, dimension) in slot order (fixed,
+// so a frame's vector does not depend on what else was encoded with it),
+// forms u and v, takes sign(z) sqrt|z|, and the block writes its [32][8]
+// tiles through shared memory (runs of 8 contiguous floats); the block's sum
+// of squares goes to sq. Kernel B: one block per frame sums the block squares
+// (in FP64, fixed order) and scales the frame's vector by 1/||z||.
 //
-// FP32 form slots hold centred sums [A = sum g (x-mu) (D), B = sum g (x-mu)^2
-// (D), S0]: u = A/sigma alpha/N, v = (B/sigma^2 - S0) beta/N.
-// BF16 form slots hold raw moments [S1 (D), S2hi (D), S2lo (D), S0] and the
-// centring happens here in FP64:
-//   u = (S1 - mu S0) / sigma * alpha / N
-//   v = ((S2 - 2 mu S1 + mu^2 S0) / sigma^2 - S0) * beta / N.
+// All per-element arithmetic is FP32 (GB300's FP64 rate is a small fraction
+// of its FP32 rate). The BF16 form's raw moments are centred with FMAs whose
+// rounding is relative to the centred quantities:
+//   a  = S1 - mu S0                  = fma(-mu, S0, S1)
+//   b  = S2 - mu S1                  = fma(-mu, S1, S2hi) + S2lo
+//   M2 = S2 - 2 mu S1 + mu^2 S0      = b - mu a = fma(-mu, a, b)
+//   u  = a / sigma * alpha / N,   v = (M2 / sigma^2 - S0) * beta / N.
+// FP32 form slots hold centred sums A = sum g (x-mu), B = sum g (x-mu)^2:
+//   u = A / sigma * alpha / N,    v = (B / sigma^2 - S0) * beta / N.
 #include "fv_internal.h"
 
 namespace fv {
 
 namespace {
 
-constexpr int FA_THREADS = 128;
+constexpr int FA_THREADS = 256;   // 32 components x 8 dimension lanes
 constexpr int FB_THREADS = 256;
 
-__device__ __forceinline__ double ssqrt(double v) { return v > 0.0 ? sqrt(v) : (v < 0.0 ? -sqrt(-v) : 0.0); }
+__device__ __forceinline__ float ssqrtf(float v) { return v > 0.f ? sqrtf(v) : (v < 0.f ? -sqrtf(-v) : 0.f); }
 
+// Sum of one statistic over a frame's slots in a fixed order; four
+// interleaved partial sums keep four loads in flight.
+__device__ __forceinline__ float slot_sum(const float *p, size_t stride, int n) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int s = 0;
+    for (; s + 4 <= n; s += 4) {
+        a0 += p[(size_t)s * stride];
+        a1 += p[(size_t)(s + 1) * stride];
+        a2 += p[(size_t)(s + 2) * stride];
+        a3 += p[(size_t)(s + 3) * stride];
+    }
+    for (; s < n; ++s) a0 += p[(size_t)s * stride];
+    return (a0 + a1) + (a2 + a3);
+}
+
+// grid (Kp/32, ceil(D/8), frames); thread (lane -> component, grp -> dimension)
 template <bool RAW>
 __global__ void __launch_bounds__(FA_THREADS)
 finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, const FrameInfo *__restrict__ frames,
                   GmmDev g, double *__restrict__ sq, float *__restrict__ out) {
-    extern __shared__ double sacc[];   // [P]
-    __shared__ double red[FA_THREADS];
-    const int k = blockIdx.x, f = blockIdx.y;
+    __shared__ float tile[2][32][9];   // [u|v][component][dimension]
+    __shared__ float red[FA_THREADS];
+    const int f = blockIdx.z;
+    const int k0 = blockIdx.x * 32, d0 = blockIdx.y * 8;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int k = k0 + lane, d = d0 + grp;
     const FrameInfo fr = frames[f];
     const size_t KD = (size_t)K * D;
+    const size_t sstride = (size_t)P * Kp;
     float *o = out + (size_t)f * 2 * KD;
-    if (fr.n == 0) {
-        for (int d = threadIdx.x; d < D; d += FA_THREADS) {
-            o[(size_t)k * D + d] = 0.f;
-            o[KD + (size_t)k * D + d] = 0.f;
-        }
-        if (threadIdx.x == 0) sq[(size_t)f * K + k] = 0.0;
-        return;
-    }
-    const size_t sstride = (size_t)Kp * P;
-    for (int j = threadIdx.x; j < P; j += FA_THREADS) {
-        // four interleaved partial sums keep four loads in flight; the
-        // combination order is fixed
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        const float *p = part + ((size_t)fr.slot0 * Kp + k) * P + j;
-        int s = 0;
-        for (; s + 4 <= fr.nslots; s += 4) {
-            a0 += (double)p[(size_t)s * sstride];
-            a1 += (double)p[(size_t)(s + 1) * sstride];
-            a2 += (double)p[(size_t)(s + 2) * sstride];
-            a3 += (double)p[(size_t)(s + 3) * sstride];
-        }
-        for (; s < fr.nslots; ++s) a0 += (double)p[(size_t)s * sstride];
-        sacc[j] = (a0 + a1) + (a2 + a3);
-    }
-    __syncthreads();
-    const double S0 = sacc[P - 1];
-    const double inv_n = 1.0 / (double)fr.n;
-    const double al = g.alpha[k] * inv_n, be = g.beta[k] * inv_n;
-    double acc = 0.0;
-    for (int d = threadIdx.x; d < D; d += FA_THREADS) {
-        double u, v;
+
+    float zu = 0.f, zv = 0.f;
+    if (d < D && k < K && fr.n > 0) {
+        const float *ps = part + (size_t)fr.slot0 * sstride + k;
+        const float S0 = slot_sum(ps + (size_t)(P - 1) * Kp, sstride, fr.nslots);
+        const float s1 = slot_sum(ps + (size_t)d * Kp, sstride, fr.nslots);
+        const float s2 = slot_sum(ps + (size_t)(D + d) * Kp, sstride, fr.nslots);
+        const float inv_n = 1.0f / (float)fr.n;
+        const float al = g.alpha[k] * inv_n, be = g.beta[k] * inv_n;
+        const float isd = g.s_t[(size_t)d * Kp + k], pr = g.prec_t[(size_t)d * Kp + k];
+        float u, v;
         if (RAW) {
-            const double m = g.mu64[(size_t)k * D + d];
-            const double S1 = sacc[d];
-            const double S2 = sacc[D + d] + sacc[2 * D + d];
-            u = (S1 - m * S0) * g.isd64[(size_t)k * D + d] * al;
-            v = ((S2 - 2.0 * m * S1 + m * m * S0) * g.prec64[(size_t)k * D + d] - S0) * be;
+            const float s3 = slot_sum(ps + (size_t)(2 * D + d) * Kp, sstride, fr.nslots);
+            const float m = g.mu_t[(size_t)d * Kp + k];
+            const float a = fmaf(-m, S0, s1);
+            const float b = fmaf(-m, s1, s2) + s3;
+            const float m2 = fmaf(-m, a, b);
+            u = a * isd * al;
+            v = fmaf(m2, pr, -S0) * be;
         } else {
-            u = sacc[d] * g.isd64[(size_t)k * D + d] * al;
-            v = (sacc[D + d] * g.prec64[(size_t)k * D + d] - S0) * be;
+            u = s1 * isd * al;
+            v = fmaf(s2, pr, -S0) * be;
         }
-        const double zu = ssqrt(u), zv = ssqrt(v);
-        o[(size_t)k * D + d] = (float)zu;
-        o[KD + (size_t)k * D + d] = (float)zv;
-        acc += zu * zu + zv * zv;
+        zu = ssqrtf(u);
+        zv = ssqrtf(v);
     }
-    red[threadIdx.x] = acc;
+    tile[0][lane][grp] = zu;
+    tile[1][lane][grp] = zv;
+    red[threadIdx.x] = fmaf(zu, zu, zv * zv);
     __syncthreads();
+    // stores: 8 consecutive dimensions of one component per 8 lanes
+    {
+        const int dd = threadIdx.x & 7, kk = threadIdx.x >> 3;   // 32 components x 8 dimensions
+        const int kw = k0 + kk, dw = d0 + dd;
+        if (kw < K && dw < D) {
+            o[(size_t)kw * D + dw] = tile[0][kk][dd];
+            o[KD + (size_t)kw * D + dw] = tile[1][kk][dd];
+        }
+    }
     for (int s = FA_THREADS / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) sq[(size_t)f * K + k] = red[0];
+    if (threadIdx.x == 0) sq[((size_t)f * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (double)red[0];
 }
 
 __global__ void __launch_bounds__(FB_THREADS)
-finalize_b_kernel(int K, int D, const double *__restrict__ sq, float *__restrict__ out,
+finalize_b_kernel(int K, int D, int nb, const double *__restrict__ sq, float *__restrict__ out,
                   const uint32_t *__restrict__ err) {
-    __shared__ double red[FB_THREADS];
+    __shared__ double tot_s;
     const int f = blockIdx.x;
-    double a = 0.0;
-    for (int k = threadIdx.x; k < K; k += FB_THREADS) a += sq[(size_t)f * K + k];
-    red[threadIdx.x] = a;
-    __syncthreads();
-    for (int s = FB_THREADS / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += sq[(size_t)f * nb + b];
+        tot_s = t;
     }
-    const double tot = red[0];
+    __syncthreads();
+    const double tot = tot_s;
     const size_t n = (size_t)2 * K * D;
     float *o = out + (size_t)f * n;
     if (err && *err) {   // an earlier kernel of this call gave up: poison the output
@@ -121,28 +136,20 @@ finalize_b_kernel(int K, int D, const double *__restrict__ sq, float *__restrict
 cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments, const FrameInfo *frames,
                             int B, double *sq, float *out, cudaStream_t st, const uint32_t *err) {
     if (B <= 0) return cudaSuccess;
-    dim3 grid_a((unsigned)g->K, (unsigned)B);
-    const size_t smem = sizeof(double) * P;
+    const int nbx = g->Kp / 32, nby = (g->D + 7) / 8, nb = nbx * nby;
+    dim3 grid_a((unsigned)nbx, (unsigned)nby, (unsigned)B);
     if (raw_moments) {
-        cudaError_t e = cudaFuncSetAttribute(finalize_a_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        {
         KernelTimer kt_("finalize_a", st);
-        finalize_a_kernel<true><<<grid_a, FA_THREADS, smem, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out);
-    }
+        finalize_a_kernel<true><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out);
     } else {
-        cudaError_t e = cudaFuncSetAttribute(finalize_a_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        {
         KernelTimer kt_("finalize_a", st);
-        finalize_a_kernel<false><<<grid_a, FA_THREADS, smem, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out);
-    }
+        finalize_a_kernel<false><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     {
         KernelTimer kt_("finalize_b", st);
-        finalize_b_kernel<<<(unsigned)B, FB_THREADS, 0, st>>>(g->K, g->D, sq, out, err);
+        finalize_b_kernel<<<(unsigned)B, FB_THREADS, 0, st>>>(g->K, g->D, nb, sq, out, err);
     }
     return cudaGetLastError();
 }

@@ -224,19 +224,17 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
         buf ^= 1;
     }
     if (!active) return;
-    float *dst = part + (size_t)u.slot * Kp * P;
+    // slot layout part[slot][j][Kp]: this thread's 4 components are contiguous
+    float *dst = part + (size_t)u.slot * Kp * P + kb;
 #pragma unroll
-    for (int c = 0; c < S_CPT; ++c) {
-        float *row = dst + (size_t)(kb + c) * P;
-#pragma unroll
-        for (int j = 0; j < S_DPT; ++j) {
-            if (db + j < D) {
-                row[db + j] = U[c][j];
-                row[D + db + j] = W[c][j];
-            }
+    for (int j = 0; j < S_DPT; ++j) {
+        if (db + j < D) {
+            *reinterpret_cast<float4 *>(dst + (size_t)(db + j) * Kp) = make_float4(U[0][j], U[1][j], U[2][j], U[3][j]);
+            *reinterpret_cast<float4 *>(dst + (size_t)(D + db + j) * Kp) =
+                make_float4(W[0][j], W[1][j], W[2][j], W[3][j]);
         }
-        if (db == 0) row[2 * D] = S0[c];
     }
+    if (db == 0) *reinterpret_cast<float4 *>(dst + (size_t)(2 * D) * Kp) = make_float4(S0[0], S0[1], S0[2], S0[3]);
 }
 
 }  // namespace

@@ -54,16 +54,17 @@ struct GmmDev {
     float *cst;      // [Kp]     log w - 1/2 sum_d log sigma^2 (-inf on padding)
     float *s_kd;     // [Kp][Dp] 1/sigma, dimension-contiguous (statistics)
     float *mu_kd;    // [Kp][Dp] mu (statistics: t = (x - mu) / sigma)
-    // shared by both forms (finalise)
-    double *alpha;   // [K] 1/sqrt(w)
-    double *beta;    // [K] 1/sqrt(2w)
-    double *mu64;    // [K][D]
-    double *isd64;   // [K][D] 1/sigma
-    double *prec64;  // [K][D] 1/sigma^2
+    // shared by both forms (finalise), component-contiguous, FP32 rounded from
+    // FP64 (zero on padding); 1/sigma of the finalise is s_t
+    float *mu_t;     // [D][Kp] mu
+    float *prec_t;   // [D][Kp] 1/sigma^2
+    float *alpha;    // [Kp] 1/sqrt(w)
+    float *beta;     // [Kp] 1/sqrt(2w)
     // BF16 form: B operands of the log-likelihood GEMM, [term][Kp][D16] bf16,
     // terms = Q_hi, Q_lo, R_hi, R_lo with Q = mu/sigma^2, R = -1/(2 sigma^2)
     uint16_t *bimg;
     float *cfull;    // [Kp] log w - 1/2 sum log sigma^2 - 1/2 sum mu^2/sigma^2 (FP64 -> FP32; -inf on padding)
+    float *cl2;      // [Kp] cfull * log2(e), formed in FP64
 };
 
 }  // namespace fv
@@ -103,9 +104,11 @@ cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows,
 cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
                              int n_units, float *part, int P, cudaStream_t st);
 
+// Statistics slots are component-fastest: part[slot][j][Kp], j < P.
 // Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,
 // L2. raw_moments selects the BF16 form's [S1, S2hi, S2lo, S0] layout
-// (P = 3D+1) over the FP32 form's centred [U, sum g t^2, S0] (P = 2D+1).
+// (P = 3D+1) over the FP32 form's centred [A, B, S0] layout (P = 2D+1).
+// sq needs B * (Kp / 32) * ceil(D / 8) doubles.
 // err (nullable): device error word of the call; when a kernel set it, every
 // output element becomes NaN so a failed encode can never look valid.
 cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments,

@@ -66,9 +66,9 @@ __global__ void noalloc_plan_kernel(int64_t n, int64_t rpr, int nslots, FrameInf
 
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
-size_t scratch_bytes(int64_t N, int Kp, int K, int P, int64_t nslots) {
+size_t scratch_bytes(int64_t N, int Kp, int K, int D, int P, int64_t nslots) {
     return al256(sizeof(float) * (size_t)N * Kp) + al256(sizeof(float) * (size_t)nslots * Kp * P) +
-           al256(sizeof(FrameInfo)) + al256(sizeof(StatUnit) * (size_t)nslots) + al256(sizeof(double) * K);
+           al256(sizeof(FrameInfo)) + al256(sizeof(StatUnit) * (size_t)nslots) + al256(sizeof(double) * (size_t)(Kp / 32) * ((D + 7) / 8));
 }
 
 bool device_pointer(const void *p) {
@@ -104,11 +104,11 @@ extern "C" int fv_encode_noalloc(const fv_gmm *gmm, const float *X, int64_t N, f
     const int64_t per_range = (int64_t)(Kp / 64) * ((D + 63) / 64);
     int64_t rpr = std::max<int64_t>(64, round_up64((rows * per_range + 3LL * sms - 1) / (3LL * sms), 32));
     int64_t nslots = (rows + rpr - 1) / rpr;
-    while (scratch_bytes(rows, Kp, K, P, nslots) > kNoAllocScratchBytes && nslots > 1) {
+    while (scratch_bytes(rows, Kp, K, D, P, nslots) > kNoAllocScratchBytes && nslots > 1) {
         rpr *= 2;
         nslots = (rows + rpr - 1) / rpr;
     }
-    if (scratch_bytes(rows, Kp, K, P, nslots) > kNoAllocScratchBytes)
+    if (scratch_bytes(rows, Kp, K, D, P, nslots) > kNoAllocScratchBytes)
         return fail(FV_ERR_UNSUPPORTED,
                     "fv_encode_noalloc: N=" + std::to_string(N) + " with K=" + std::to_string(K) + ", D=" +
                         std::to_string(D) + " needs more than the fixed 32 MiB scratch (posteriors alone take N*" +

@@ -58,6 +58,8 @@ __global__ void prep_kernel(int K, int D, int Kp, int Dp, int D16, const float *
         for (int d = threadIdx.x; d < D; d += blockDim.x) {
             g.s_t[(size_t)d * Kp + k] = 0.f;
             g.nms_t[(size_t)d * Kp + k] = 0.f;
+            g.mu_t[(size_t)d * Kp + k] = 0.f;
+            g.prec_t[(size_t)d * Kp + k] = 0.f;
         }
         for (int d = threadIdx.x; d < Dp; d += blockDim.x) {
             g.s_kd[(size_t)k * Dp + d] = 0.f;
@@ -69,6 +71,9 @@ __global__ void prep_kernel(int K, int D, int Kp, int Dp, int D16, const float *
         if (threadIdx.x == 0) {
             g.cst[k] = -INFINITY;
             if (g.cfull) g.cfull[k] = -INFINITY;
+            if (g.cl2) g.cl2[k] = -INFINITY;
+            g.alpha[k] = 0.f;
+            g.beta[k] = 0.f;
         }
         return;
     }
@@ -86,9 +91,8 @@ __global__ void prep_kernel(int K, int D, int Kp, int Dp, int D16, const float *
             g.nms_t[(size_t)d * Kp + k] = (float)(-m * isd);
             g.s_kd[(size_t)k * Dp + d] = (float)isd;
             g.mu_kd[(size_t)k * Dp + d] = (float)m;
-            g.mu64[(size_t)k * D + d] = m;
-            g.isd64[(size_t)k * D + d] = isd;
-            g.prec64[(size_t)k * D + d] = p;
+            g.mu_t[(size_t)d * Kp + k] = (float)m;
+            g.prec_t[(size_t)d * Kp + k] = (float)p;
             if (g.bimg) {
                 const double q = m * p, r = -0.5 * p;
                 const uint16_t qh = bf16_bits((float)q), rh = bf16_bits((float)r);
@@ -115,8 +119,9 @@ __global__ void prep_kernel(int K, int D, int Kp, int Dp, int D16, const float *
         const double c1 = log(wk) - 0.5 * slog;
         g.cst[k] = (float)c1;
         if (g.cfull) g.cfull[k] = (float)(c1 - 0.5 * smq);
-        g.alpha[k] = 1.0 / sqrt(wk);
-        g.beta[k] = 1.0 / sqrt(2.0 * wk);
+        if (g.cl2) g.cl2[k] = (float)((c1 - 0.5 * smq) * 1.4426950408889634);
+        g.alpha[k] = (float)(1.0 / sqrt(wk));
+        g.beta[k] = (float)(1.0 / sqrt(2.0 * wk));
     }
 }
 
@@ -191,13 +196,13 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     const size_t o_s_t = take(sizeof(float) * D * Kp), o_nms_t = take(sizeof(float) * D * Kp);
     const size_t o_cst = take(sizeof(float) * Kp);
     const size_t o_s_kd = take(sizeof(float) * Kp * Dp), o_mu_kd = take(sizeof(float) * Kp * Dp);
-    const size_t o_alpha = take(sizeof(double) * K), o_beta = take(sizeof(double) * K);
-    const size_t o_mu = take(sizeof(double) * K * D), o_isd = take(sizeof(double) * K * D);
-    const size_t o_prec = take(sizeof(double) * K * D);
-    size_t o_bimg = 0, o_cfull = 0;
+    const size_t o_alpha = take(sizeof(float) * Kp), o_beta = take(sizeof(float) * Kp);
+    const size_t o_mu = take(sizeof(float) * D * Kp), o_prec = take(sizeof(float) * D * Kp);
+    size_t o_bimg = 0, o_cfull = 0, o_cl2 = 0;
     if (precision == FV_PREC_BF16) {
         o_bimg = take(sizeof(uint16_t) * 4 * Kp * D16);
         o_cfull = take(sizeof(float) * Kp);
+        o_cl2 = take(sizeof(float) * Kp);
     }
     const size_t o_in = take(sizeof(float) * (K + 2 * (size_t)K * D));
     char *base = nullptr;
@@ -214,13 +219,13 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     d.cst = (float *)(base + o_cst);
     d.s_kd = (float *)(base + o_s_kd);
     d.mu_kd = (float *)(base + o_mu_kd);
-    d.alpha = (double *)(base + o_alpha);
-    d.beta = (double *)(base + o_beta);
-    d.mu64 = (double *)(base + o_mu);
-    d.isd64 = (double *)(base + o_isd);
-    d.prec64 = (double *)(base + o_prec);
+    d.alpha = (float *)(base + o_alpha);
+    d.beta = (float *)(base + o_beta);
+    d.mu_t = (float *)(base + o_mu);
+    d.prec_t = (float *)(base + o_prec);
     d.bimg = precision == FV_PREC_BF16 ? (uint16_t *)(base + o_bimg) : nullptr;
     d.cfull = precision == FV_PREC_BF16 ? (float *)(base + o_cfull) : nullptr;
+    d.cl2 = precision == FV_PREC_BF16 ? (float *)(base + o_cl2) : nullptr;
     float *in = (float *)(base + o_in);
 
     cudaStream_t st;
