@@ -130,9 +130,49 @@ bool is_device_ptr(const void *p) {
 struct Plan {
     std::vector<FrameInfo> frames;
     std::vector<StatUnit> units;
+    std::vector<int2> cta;   // BF16 statistics: (first unit, count) per persistent CTA
     int64_t rows = 0;
     int nonempty = 0;
 };
+
+// Split the packed rows into G near-equal shares (boundaries on 64-row
+// multiples) and cut each share at frame boundaries: every piece is a unit
+// with its own slot. A frame's units come out consecutive, in row order.
+void make_plan_balanced(const int64_t *offsets, int B, int G, Plan &p) {
+    p.frames.resize(B);
+    p.units.clear();
+    p.cta.clear();
+    p.rows = offsets[B];
+    p.nonempty = 0;
+    for (int b = 0; b < B; ++b) {
+        p.frames[b].row0 = offsets[b];
+        p.frames[b].n = offsets[b + 1] - offsets[b];
+        p.frames[b].slot0 = 0;
+        p.frames[b].nslots = 0;
+        if (p.frames[b].n > 0) ++p.nonempty;
+    }
+    const int64_t R = p.rows;
+    int f = 0;
+    int64_t a = 0;
+    for (int c = 0; c < G; ++c) {
+        const int64_t e = (c == G - 1) ? R : std::max<int64_t>(a, (R * (c + 1) / G) / 64 * 64);
+        const int first = (int)p.units.size();
+        while (f < B && offsets[f + 1] <= a) ++f;
+        for (int ff = f; ff < B && offsets[ff] < e; ++ff) {
+            const int64_t s0 = std::max(a, offsets[ff]), s1 = std::min(e, offsets[ff + 1]);
+            if (s1 <= s0) continue;
+            StatUnit u;
+            u.row0 = s0;
+            u.nrows = (int32_t)(s1 - s0);
+            u.slot = (int32_t)p.units.size();
+            if (p.frames[ff].nslots == 0) p.frames[ff].slot0 = u.slot;
+            ++p.frames[ff].nslots;
+            p.units.push_back(u);
+        }
+        p.cta.push_back(make_int2(first, (int)p.units.size() - first));
+        a = e;
+    }
+}
 
 // Split every frame into row ranges of at most `rpr` rows; each range becomes
 // one statistics unit writing its own slot (the paper's per-block copies).
@@ -186,18 +226,19 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     const int sms = device_sms(g->device);
     const bool bf16 = g->prec == FV_PREC_BF16;
 
-    // rows per statistics range: aim for about three blocks per SM in one wave
-    int64_t rpr;
-    if (bf16) {
-        rpr = bf16_rows_per_range(g, rows, sms);
-    } else {
-        const int64_t blocks_per_range = (int64_t)(Kp / 64) * ((D + 63) / 64);
-        rpr = (rows * blocks_per_range + 3LL * sms - 1) / (3LL * sms);
-        rpr = std::min<int64_t>(std::max<int64_t>(round_up64(rpr, 32), 64), 16384);
-    }
     Plan plan;
-    make_plan(offsets, B, rpr, plan);
+    if (bf16) {
+        // persistent statistics CTAs over balanced shares of the packed rows
+        make_plan_balanced(offsets, B, bf16_stat_ctas(g, rows, sms), plan);
+    } else {
+        // rows per statistics range: aim for about three blocks per SM in one wave
+        const int64_t blocks_per_range = (int64_t)(Kp / 64) * ((D + 63) / 64);
+        int64_t rpr = (rows * blocks_per_range + 3LL * sms - 1) / (3LL * sms);
+        rpr = std::min<int64_t>(std::max<int64_t>(round_up64(rpr, 32), 64), 16384);
+        make_plan(offsets, B, rpr, plan);
+    }
     const int nslots = (int)plan.units.size();
+    const int nctas = (int)plan.cta.size();
     const int P = bf16 ? 3 * D + 1 : 2 * D + 1;
     const int64_t ldx_dev = bf16 ? (x_bf16 ? ld_x : (int64_t)g->Dp) : (int64_t)D;
 
@@ -209,6 +250,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     const size_t o_part = s.take(sizeof(float) * std::max(nslots, 1) * (size_t)Kp * P);
     const size_t o_fr = s.take(sizeof(FrameInfo) * B);
     const size_t o_un = s.take(sizeof(StatUnit) * std::max(nslots, 1));
+    const size_t o_cta = s.take(sizeof(int2) * std::max(nctas, 1));
     const size_t o_sq = s.take(sizeof(double) * (size_t)B * (Kp / 32) * ((D + 7) / 8));
     const size_t o_err = s.take(sizeof(uint32_t));
     const size_t o_out = !out_on_device ? s.take(sizeof(float) * fvlen * B) : 0;
@@ -231,8 +273,10 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
         float *outd = out_on_device ? fv_out : (float *)(s.base + o_out);
         FrameInfo *frd = (FrameInfo *)(s.base + o_fr);
         StatUnit *und = (StatUnit *)(s.base + o_un);
+        int2 *ctad = (int2 *)(s.base + o_cta);
         if ((e = stage_upload(frd, plan.frames.data(), sizeof(FrameInfo) * B, st)) != cudaSuccess ||
-            (e = stage_upload(und, plan.units.data(), sizeof(StatUnit) * nslots, st)) != cudaSuccess) {
+            (e = stage_upload(und, plan.units.data(), sizeof(StatUnit) * nslots, st)) != cudaSuccess ||
+            (e = stage_upload(ctad, plan.cta.data(), sizeof(int2) * nctas, st)) != cudaSuccess) {
             rc = cuda_fail(e, "work-list upload");
             break;
         }
@@ -264,7 +308,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
                 xb = xconv;
             }
             uint16_t *gam = (uint16_t *)(s.base + o_gam);
-            rc = run_bf16_encoder(g, xb, ldx_dev, rows, gam, und, nslots, part, P, sms, errd, st);
+            rc = run_bf16_encoder(g, xb, ldx_dev, rows, gam, und, ctad, nctas, part, P, sms, errd, st);
             if (rc != FV_OK) break;
         }
         if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd)) != cudaSuccess) {

@@ -50,6 +50,7 @@ constexpr int kPostThreads = 384;      // posteriors kernel: 12 warps
 constexpr int kTileRows = 128;         // posteriors tile (MMA M)
 constexpr int kStatRows = 64;          // statistics stage rows
 constexpr int kStatStages = 3;
+constexpr uint32_t kGBlk = 64u * kStatRows * 2u;   // one 64-component x 64-row gamma box (8 KB)
 constexpr float kLog2e = 1.4426950408889634f;
 
 // ---- small device helpers ---------------------------------------------------------
@@ -282,35 +283,53 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
             if (!__all_sync(0xffffffffu, mbar_wait(&bars[PB_LFULL + b], (i >> 1) & 1, abort_flag, p.err))) break;
             tc_fence_after();
             const uint32_t ta = lane_base + (uint32_t)(b * p.ncta);
-            float v[32];
             float m = -INFINITY, z = 0.f;
             float mc[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t ra[32], rb[32];
+            // software pipeline: the next chunk's TMEM load is in flight while
+            // this chunk is processed; this chunk's constants are requested
+            // before waiting on its TMEM load
+            tmem_ld32_issue(ta + c0 * 32, ra);
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 if (cc >= nh) break;
                 const int c = c0 + cc;
-                tmem_ld32(ta + c * 32, v);
-                const float4 *c4 = reinterpret_cast<const float4 *>(cl + c * 32);
-                float cm = -INFINITY;
+                uint32_t(&cur)[32] = (cc & 1) ? rb : ra;
+                uint32_t(&nxt)[32] = (cc & 1) ? ra : rb;
+                float4 ccur[8];
+#pragma unroll
+                for (int k4 = 0; k4 < 8; ++k4) ccur[k4] = __ldg(reinterpret_cast<const float4 *>(cl + c * 32) + k4);
+                tmem_ld_wait(cur);
+                if (cc + 1 < nh) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
+                float y[32];
+                float cm0 = -INFINITY, cm1 = -INFINITY;
 #pragma unroll
                 for (int k4 = 0; k4 < 8; ++k4) {
-                    const float4 cv = __ldg(c4 + k4);
-                    v[4 * k4 + 0] = fmaf(v[4 * k4 + 0], kLog2e, cv.x);
-                    v[4 * k4 + 1] = fmaf(v[4 * k4 + 1], kLog2e, cv.y);
-                    v[4 * k4 + 2] = fmaf(v[4 * k4 + 2], kLog2e, cv.z);
-                    v[4 * k4 + 3] = fmaf(v[4 * k4 + 3], kLog2e, cv.w);
-                    cm = fmaxf(cm, fmaxf(fmaxf(v[4 * k4 + 0], v[4 * k4 + 1]), fmaxf(v[4 * k4 + 2], v[4 * k4 + 3])));
+                    y[4 * k4 + 0] = fmaf(__uint_as_float(cur[4 * k4 + 0]), kLog2e, ccur[k4].x);
+                    y[4 * k4 + 1] = fmaf(__uint_as_float(cur[4 * k4 + 1]), kLog2e, ccur[k4].y);
+                    y[4 * k4 + 2] = fmaf(__uint_as_float(cur[4 * k4 + 2]), kLog2e, ccur[k4].z);
+                    y[4 * k4 + 3] = fmaf(__uint_as_float(cur[4 * k4 + 3]), kLog2e, ccur[k4].w);
+                    cm0 = fmaxf(cm0, fmaxf(y[4 * k4 + 0], y[4 * k4 + 1]));
+                    cm1 = fmaxf(cm1, fmaxf(y[4 * k4 + 2], y[4 * k4 + 3]));
                 }
-                const float mn = fmaxf(m, cm);
+                const float mn = fmaxf(m, fmaxf(cm0, cm1));
                 const float mref = (mn == -INFINITY) ? 0.f : mn;
-                z *= ex2_approx(m - mref);
+                float z0 = z * ex2_approx(m - mref), z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const float e = ex2_approx(v[k] - mref);
-                    v[k] = e;
-                    z += e;
+                for (int k = 0; k < 32; k += 4) {
+                    const float e0 = ex2_approx(y[k + 0] - mref), e1 = ex2_approx(y[k + 1] - mref);
+                    const float e2 = ex2_approx(y[k + 2] - mref), e3 = ex2_approx(y[k + 3] - mref);
+                    z0 += e0;
+                    z1 += e1;
+                    z2 += e2;
+                    z3 += e3;
+                    cur[k + 0] = __float_as_uint(e0);
+                    cur[k + 1] = __float_as_uint(e1);
+                    cur[k + 2] = __float_as_uint(e2);
+                    cur[k + 3] = __float_as_uint(e3);
                 }
-                tmem_st32(ta + c * 32, v);
+                z = (z0 + z1) + (z2 + z3);
+                tmem_st32_u(ta + c * 32, cur);
                 mc[cc] = mref;
                 m = mn;
             }
@@ -343,24 +362,28 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
                 Mref = M2ref;
             }
             const float inv = 1.0f / Z;
-            // pass B: normalised posteriors -> bf16 global
+            // pass B: normalised posteriors -> bf16 global (next chunk's load in flight)
             const int64_t row = (int64_t)tile * kTileRows + r;
             uint16_t *g = p.gamma + row * p.Kp + rank * p.ncta;
+            tmem_ld32_issue(ta + c0 * 32, ra);
+            tmem_ld_wait(ra);
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 if (cc >= nh) break;
                 const int c = c0 + cc;
-                tmem_ld32(ta + c * 32, v);
+                uint32_t(&cur)[32] = (cc & 1) ? rb : ra;
+                uint32_t(&nxt)[32] = (cc & 1) ? ra : rb;
+                if (cc + 1 < nh) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
                 const float sc = ex2_approx(mc[cc] - Mref) * inv;
-                if (row < p.rows) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(g + c * 32);
+                if (row < p.rows) {   // 64 bytes of the row: two full 32-byte sectors
+                    uint32_t pk[16];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        dst[k] = make_uint4(pack_bf16x2(v[8 * k + 0] * sc, v[8 * k + 1] * sc),
-                                            pack_bf16x2(v[8 * k + 2] * sc, v[8 * k + 3] * sc),
-                                            pack_bf16x2(v[8 * k + 4] * sc, v[8 * k + 5] * sc),
-                                            pack_bf16x2(v[8 * k + 6] * sc, v[8 * k + 7] * sc));
+                    for (int k = 0; k < 16; ++k)
+                        pk[k] = pack_bf16x2(__uint_as_float(cur[2 * k]) * sc, __uint_as_float(cur[2 * k + 1]) * sc);
+                    st_global_v8(g + c * 32, pk);
+                    st_global_v8(g + c * 32 + 16, pk + 8);
                 }
+                if (cc + 1 < nh) tmem_ld_wait(nxt);
             }
             tc_fence_before();
             __syncwarp();
@@ -386,6 +409,7 @@ struct StatArgs {
     int P;         // 3D + 1 floats per component in a slot
     uint32_t tmem_cols;
     const StatUnit *units;
+    const int2 *cta_units;   // per CTA: (first unit, number of units)
     float *part;
     uint32_t *err;
 };
@@ -403,8 +427,12 @@ __host__ __device__ inline StatSmem stat_smem(int nkb, int sc) {
     s.total = s.misc + 16u;
     return s;
 }
-enum { SB_FULL = 0, SB_READY = 3, SB_EMPTY = 6, SB_DONE = 9 };
+enum { SB_FULL = 0, SB_READY = 3, SB_EMPTY = 6, SB_DONE = 9, SB_TEMPTY = 10, SB_DRAIN = 11 };
 
+// Persistent: CTA (blockIdx.x, blockIdx.y) walks its units (row segments of
+// one frame, contiguous in the packed rows) through one continuous ring of
+// 64-row stages for the component group blockIdx.y; after each unit the
+// accumulator is flushed from TMEM to the unit's slot.
 __global__ void __launch_bounds__(kThreads, 1)
 bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmX, StatArgs p) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -417,10 +445,9 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
         if (threadIdx.x == 0) atomicOr(p.err, kErrAlign);
         return;
     }
-    const StatUnit u = p.units[blockIdx.x];
+    const int2 cu = p.cta_units[blockIdx.x];
     const int kc0 = blockIdx.y * p.sc;
     const int nchunk = p.sc / 128;
-    const int nit = (u.nrows + kStatRows - 1) / kStatRows;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStatStages; ++s) {
@@ -429,6 +456,8 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
             mbar_init(&bars[SB_EMPTY + s], 1);
         }
         mbar_init(&bars[SB_DONE], 1);
+        mbar_init(&bars[SB_TEMPTY], 4);
+        mbar_init(&bars[SB_DRAIN], 1);
         misc[1] = 0u;
         fence_mbar_init();
     }
@@ -447,16 +476,26 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
         prefetch_tmap(&tmG);
         prefetch_tmap(&tmX);
         int last_use[kStatStages] = {-1, -1, -1};
-        for (int it = 0; it < nit; ++it) {
-            const int s = it % kStatStages, use = it / kStatStages;
-            if (use > 0 && !mbar_wait(&bars[SB_EMPTY + s], (use - 1) & 1, abort_flag, p.err)) break;
-            uint8_t *sg = smem + s * L.stage;
-            uint8_t *sy = sg + L.g_stage;
-            const int y = (int)(u.row0 + (int64_t)it * kStatRows);
-            mbar_arrive_expect_tx(&bars[SB_FULL + s], (uint32_t)(p.sc / 16 + p.nkb) * blk);
-            for (int cb = 0; cb < p.sc / 16; ++cb) tma_load_2d(sg + cb * blk, &tmG, &bars[SB_FULL + s], kc0 + cb * 16, y);
-            for (int j = 0; j < p.nkb; ++j) tma_load_2d(sy + j * blk, &tmX, &bars[SB_FULL + s], j * 16, y);
-            last_use[s] = use;
+        int gs = 0;
+        bool ok = true;
+        for (int ui = 0; ok && ui < cu.y; ++ui) {
+            const StatUnit u = p.units[cu.x + ui];
+            const int nit = (u.nrows + kStatRows - 1) / kStatRows;
+            for (int it = 0; it < nit; ++it, ++gs) {
+                const int s = gs % kStatStages, use = gs / kStatStages;
+                if (use > 0 && !mbar_wait(&bars[SB_EMPTY + s], (use - 1) & 1, abort_flag, p.err)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *sg = smem + s * L.stage;
+                uint8_t *sy = sg + L.g_stage;
+                const int y = (int)(u.row0 + (int64_t)it * kStatRows);
+                mbar_arrive_expect_tx(&bars[SB_FULL + s], (uint32_t)(p.sc / 16 + p.nkb) * blk);
+                for (int cb = 0; cb < p.sc / 64; ++cb)   // 64 components x 64 rows, 128-byte rows
+                    tma_load_2d(sg + cb * kGBlk, &tmG, &bars[SB_FULL + s], kc0 + cb * 64, y);
+                for (int j = 0; j < p.nkb; ++j) tma_load_2d(sy + j * blk, &tmX, &bars[SB_FULL + s], j * 16, y);
+                last_use[s] = use;
+            }
         }
         for (int s = 0; s < kStatStages; ++s) {
             if (last_use[s] < 0) continue;
@@ -467,70 +506,98 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_bf16(128, p.ny, true, true);
-        bool issued = false;
-        for (int it = 0; it < nit; ++it) {
-            const int s = it % kStatStages;
-            if (!mbar_wait(&bars[SB_READY + s], (it / kStatStages) & 1, abort_flag, p.err)) break;
-            tc_fence_after();
-            const uint32_t sg = smem_u32(smem + s * L.stage);
-            const uint32_t sy = sg + L.g_stage;
-            for (int q = 0; q < kStatRows / 16; ++q) {
-                for (int c = 0; c < nchunk; ++c) {
-                    const uint64_t a = sdesc_sw32(sg + c * 8 * blk + q * 512, blk, 256);
-                    const uint64_t b = sdesc_sw32(sy + q * 512, blk, 256);
-                    mma_bf16(tmem + (uint32_t)(c * p.ny), a, b, idesc, (it > 0 || q > 0) ? 1u : 0u);
-                }
+        bool issued = false, ok = true;
+        int gs = 0;
+        for (int ui = 0; ok && ui < cu.y; ++ui) {
+            const StatUnit u = p.units[cu.x + ui];
+            const int nit = (u.nrows + kStatRows - 1) / kStatRows;
+            if (ui > 0) {   // the epilogue has read the previous unit's accumulator
+                if (!mbar_wait(&bars[SB_TEMPTY], (ui - 1) & 1, abort_flag, p.err)) break;
+                tc_fence_after();
             }
-            mma_commit(&bars[SB_EMPTY + s]);
-            issued = true;
+            for (int it = 0; it < nit; ++it, ++gs) {
+                const int s = gs % kStatStages;
+                if (!mbar_wait(&bars[SB_READY + s], (gs / kStatStages) & 1, abort_flag, p.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sg = smem_u32(smem + s * L.stage);
+                const uint32_t sy = sg + L.g_stage;
+                for (int q = 0; q < kStatRows / 16; ++q) {
+                    for (int c = 0; c < nchunk; ++c) {
+                        // gamma^T, MN-major, 128-byte swizzle: 64-component blocks kGBlk
+                        // apart, 8-row groups 1024 B apart, 16 rows per K step
+                        const uint64_t a = sdesc_sw128(sg + c * 2 * kGBlk + q * 2048, kGBlk, 1024);
+                        const uint64_t b = sdesc_sw32(sy + q * 512, blk, 256);
+                        mma_bf16(tmem + (uint32_t)(c * p.ny), a, b, idesc, (it > 0 || q > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit(&bars[SB_EMPTY + s]);
+                issued = true;
+            }
+            if (ok) mma_commit(&bars[SB_DONE]);
         }
-        if (issued) mma_commit(&bars[SB_DONE]);
+        if (issued) {   // every issued MMA has finished before TMEM is released
+            mma_commit(&bars[SB_DRAIN]);
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(&bars[SB_DRAIN], 0) && globaltimer() - t0 < 1000000000ull) {
+            }
+        }
     } else if (warp >= 2) {
-        // ---------------- Y builders: x (masked), x^2 hi/lo, ones ----------------
+        // ---------------- Y builders (warps 2-7); warps 4-7 also flush TMEM ----------------
         const int t = threadIdx.x - 64;          // 0..191
         const int xchunks = p.nkb * kStatRows * 2;
         const uint32_t plane = (uint32_t)p.nkb * blk;
-        for (int it = 0; it < nit; ++it) {
-            const int s = it % kStatStages;
-            if (!mbar_wait(&bars[SB_FULL + s], (it / kStatStages) & 1, abort_flag, p.err)) break;
-            uint8_t *sy = smem + s * L.stage + L.g_stage;
-            const int valid = min(kStatRows, u.nrows - it * kStatRows);
-            for (int c = t; c < xchunks; c += 192) {
-                const int row = (c >> 1) % kStatRows;   // 32-byte rows; the swizzle stays inside a row
-                uint4 x = *reinterpret_cast<const uint4 *>(sy + c * 16);
-                uint4 hi, lo;
-                if (row < valid) {
-                    square_split(x, hi, lo);
-                } else {
-                    x = make_uint4(0, 0, 0, 0);
-                    hi = x;
-                    lo = x;
-                    *reinterpret_cast<uint4 *>(sy + c * 16) = x;
+        const int D16 = p.nkb * 16;
+        int gs = 0;
+        bool ok = true;
+        for (int ui = 0; ok && ui < cu.y; ++ui) {
+            const StatUnit u = p.units[cu.x + ui];
+            const int nit = (u.nrows + kStatRows - 1) / kStatRows;
+            for (int it = 0; it < nit; ++it, ++gs) {
+                const int s = gs % kStatStages;
+                if (!mbar_wait(&bars[SB_FULL + s], (gs / kStatStages) & 1, abort_flag, p.err)) {
+                    ok = false;
+                    break;
                 }
-                *reinterpret_cast<uint4 *>(sy + plane + c * 16) = hi;
-                *reinterpret_cast<uint4 *>(sy + 2 * plane + c * 16) = lo;
+                uint8_t *sy = smem + s * L.stage + L.g_stage;
+                const int valid = min(kStatRows, u.nrows - it * kStatRows);
+                for (int c = t; c < xchunks; c += 192) {
+                    const int row = (c >> 1) % kStatRows;   // 32-byte rows; the swizzle stays inside a row
+                    uint4 x = *reinterpret_cast<const uint4 *>(sy + c * 16);
+                    uint4 hi, lo;
+                    if (row < valid) {
+                        square_split(x, hi, lo);
+                    } else {
+                        x = make_uint4(0, 0, 0, 0);
+                        hi = x;
+                        lo = x;
+                        *reinterpret_cast<uint4 *>(sy + c * 16) = x;
+                    }
+                    *reinterpret_cast<uint4 *>(sy + plane + c * 16) = hi;
+                    *reinterpret_cast<uint4 *>(sy + 2 * plane + c * 16) = lo;
+                }
+                for (int c = t; c < kStatRows * 2; c += 192) {
+                    const int row = c >> 1;
+                    const uint32_t one = row < valid ? 0x3F803F80u : 0u;   // bf16 1.0 pairs
+                    *reinterpret_cast<uint4 *>(sy + 3 * plane + c * 16) = make_uint4(one, one, one, one);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars[SB_READY + s]);
             }
-            for (int c = t; c < kStatRows * 2; c += 192) {
-                const int row = c >> 1;
-                const uint32_t one = row < valid ? 0x3F803F80u : 0u;   // bf16 1.0 pairs
-                *reinterpret_cast<uint4 *>(sy + 3 * plane + c * 16) = make_uint4(one, one, one, one);
+            if (!ok || warp < 4) continue;
+            // flush this unit's accumulator: TMEM -> slot part[slot][j][Kp]
+            const int q = warp & 3;
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[SB_DONE], ui & 1, abort_flag, p.err))) {
+                ok = false;
+                break;
             }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bars[SB_READY + s]);
-        }
-    }
-
-    // ---------------- epilogue: TMEM -> statistics slot ----------------
-    if (warp >= 4) {
-        const int q = warp & 3;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[SB_DONE], 0, abort_flag, p.err));
-        tc_fence_after();
-        if (ok) {
-            const int D16 = p.nkb * 16;
+            tc_fence_after();
             for (int c = 0; c < nchunk; ++c) {
                 const int k = kc0 + c * 128 + q * 32 + lane;
-                float *dst = p.part + (size_t)u.slot * p.Kp * p.P + k;   // part[slot][j][Kp]
+                float *dst = p.part + (size_t)u.slot * p.Kp * p.P + k;
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * p.ny);
                 for (int n0 = 0; n0 < p.ny; n0 += 32) {
                     float v[32];
@@ -548,6 +615,9 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars[SB_TEMPTY]);
         }
     }
     tc_fence_before();
@@ -586,15 +656,17 @@ cudaError_t get_encoder() {
     return g_encode ? cudaSuccess : cudaErrorNotSupported;
 }
 
-// 2D bf16 tensor map: `cols` x `rows` with row pitch `pitch_elems`, box 16 x box_rows,
-// 32-byte swizzle, zero fill out of bounds.
-bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t pitch_elems, uint32_t box_rows) {
+// 2D bf16 tensor map: `cols` x `rows` with row pitch `pitch_elems`, box
+// 16 x box_rows with the 32-byte swizzle, or 64 x box_rows with the 128-byte
+// swizzle when wide; zero fill out of bounds.
+bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t pitch_elems, uint32_t box_rows,
+              bool wide = false) {
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {pitch_elems * 2};
-    cuuint32_t box[2] = {16, box_rows};
+    cuuint32_t box[2] = {wide ? 64u : 16u, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, wide ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -627,15 +699,15 @@ bool bf16_config(const fv_gmm *g, BfCfg &c) {
 
 }  // namespace
 
-int64_t bf16_rows_per_range(const fv_gmm *g, int64_t rows, int sms) {
-    // about two waves of equal statistics CTAs (one CTA per SM), ranges of at
-    // least 256 rows (a slot is K x (3D+1) floats, so shorter ranges would cost
-    // more slot traffic than posterior reads)
+int bf16_stat_ctas(const fv_gmm *g, int64_t rows, int sms) {
+    // one persistent CTA per SM per component group, each with at least 512
+    // rows (a slot is K x (3D+1) floats; shorter shares would move more slot
+    // bytes than posterior bytes)
     const int sc = (g->Kp % 256 == 0) ? 256 : 128;
-    const int64_t per_range = g->Kp / sc;
-    int64_t rpr = (rows * per_range + 2LL * sms - 1) / std::max(1, 2 * sms);
-    rpr = round_up64(std::max<int64_t>(rpr, 256), kStatRows);
-    return std::min<int64_t>(rpr, 16384);
+    const int groups = g->Kp / sc;
+    const int per_group = std::max(1, sms / groups);
+    const int64_t by_rows = std::max<int64_t>(1, rows / 512);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(per_group, by_rows));
 }
 
 cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, uint16_t *Xb, cudaStream_t st) {
@@ -650,9 +722,9 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
 }
 
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
-                     const StatUnit *units, int n_units, float *part, int P, int sms, uint32_t *err,
-                     cudaStream_t st) {
-    if (rows <= 0 || n_units <= 0) return FV_OK;
+                     const StatUnit *units, const int2 *cta_units, int n_ctas, float *part, int P, int sms,
+                     uint32_t *err, cudaStream_t st) {
+    if (rows <= 0 || n_ctas <= 0) return FV_OK;
     if (get_encoder() != cudaSuccess) return fail(FV_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
     BfCfg c;
     if (!bf16_config(g, c)) return fail(FV_ERR_UNSUPPORTED, "BF16 form: shape does not fit the kernels' shared memory");
@@ -663,7 +735,7 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     if (!make_map(&tmX128, Xb, (uint64_t)g->D, (uint64_t)rows, (uint64_t)ldx, kTileRows) ||
         !make_map(&tmX64, Xb, (uint64_t)g->D, (uint64_t)rows, (uint64_t)ldx, kStatRows) ||
         !make_map(&tmB, g->dev.bimg, (uint64_t)nkb * 16, (uint64_t)4 * g->Kp, (uint64_t)nkb * 16, (uint32_t)c.ncta) ||
-        !make_map(&tmG, gamma, (uint64_t)g->Kp, (uint64_t)rows, (uint64_t)g->Kp, kStatRows))
+        !make_map(&tmG, gamma, (uint64_t)g->Kp, (uint64_t)rows, (uint64_t)g->Kp, kStatRows, true))
         return fail(FV_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 
     // posteriors: persistent clusters over 128-row tiles
@@ -701,7 +773,7 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     }
     if (e != cudaSuccess) return cuda_fail(e, "bf16 posteriors launch");
 
-    // statistics: one CTA per (row range, component group)
+    // statistics: persistent CTAs over balanced row shares x component groups
     StatArgs sa;
     sa.nkb = nkb;
     sa.D = g->D;
@@ -711,11 +783,12 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     sa.P = P;
     sa.tmem_cols = pow2_cols((c.sc / 128) * c.ny);
     sa.units = units;
+    sa.cta_units = cta_units;
     sa.part = part;
     sa.err = err;
     e = cudaFuncSetAttribute(bf16_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.stat_smem);
     if (e != cudaSuccess) return cuda_fail(e, "bf16 statistics: smem attribute");
-    dim3 grid((unsigned)n_units, (unsigned)(g->Kp / c.sc));
+    dim3 grid((unsigned)n_ctas, (unsigned)(g->Kp / c.sc));
     {
         KernelTimer kt_("bf16_stats", st);
         bf16_stats_kernel<<<grid, kThreads, c.stat_smem, st>>>(tmG, tmX64, sa);

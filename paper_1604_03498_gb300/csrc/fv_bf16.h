@@ -5,16 +5,18 @@
 
 namespace fv {
 
-// Rows per statistics range for the BF16 statistics kernel.
-int64_t bf16_rows_per_range(const fv_gmm *g, int64_t rows, int sms);
+// Number of persistent statistics CTAs (row shares) for `rows` packed rows.
+int bf16_stat_ctas(const fv_gmm *g, int64_t rows, int sms);
 
 // FP32 descriptors (rows x D) -> bfloat16 rows of pitch Dp (zero padded).
 cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, uint16_t *Xb, cudaStream_t st);
 
 // Posteriors and statistics of the BF16 form; returns an fv_status.
 // err: device word a kernel sets when a bounded wait gives up (zeroed by the caller).
+// units: row segments (one frame each) grouped per statistics CTA;
+// cta_units[c] = (first unit, count) of CTA c.
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
-                     const StatUnit *units, int n_units, float *part, int P, int sms, uint32_t *err,
-                     cudaStream_t st);
+                     const StatUnit *units, const int2 *cta_units, int n_ctas, float *part, int P, int sms,
+                     uint32_t *err, cudaStream_t st);
 
 }  // namespace fv
