@@ -192,13 +192,9 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
         // wait (bounded, even when aborting) for this thread's copies still in flight
         for (int s = 0; s < 2; ++s) {
             if (last_use[s] < 0) continue;
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(&bars[PB_XFULL + s], last_use[s] & 1) && globaltimer() - t0 < 100000000ull) {
-            }
+            mbar_drain(&bars[PB_XFULL + s], last_use[s] & 1, 200000000ll);
         }
-        const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait(&bars[PB_BFULL], 0) && globaltimer() - t0 < 100000000ull) {
-        }
+        mbar_drain(&bars[PB_BFULL], 0, 200000000ll);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_bf16(kTileRows, p.ncta, false, false);
@@ -236,9 +232,7 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
         }
         if (issued) {   // every issued MMA has finished before TMEM is released
             mma_commit(&bars[PB_DRAIN]);
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(&bars[PB_DRAIN], 0) && globaltimer() - t0 < 1000000000ull) {
-            }
+            mbar_drain(&bars[PB_DRAIN], 0, 2000000000ll);
         }
     } else if (warp == 2 || warp == 3) {
         // ---------------- x^2 hi/lo builders ----------------
@@ -406,7 +400,7 @@ struct StatArgs {
     int Kp;
     int sc;        // components per CTA (128 or 256)
     int ny;        // 3*D16 + 16 columns of Y
-    int P;         // 3D + 1 floats per component in a slot
+    int P;         // 3*D16 + 1 floats per component in a slot
     uint32_t tmem_cols;
     const StatUnit *units;
     const int2 *cta_units;   // per CTA: (first unit, number of units)
@@ -499,9 +493,7 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
         }
         for (int s = 0; s < kStatStages; ++s) {
             if (last_use[s] < 0) continue;
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(&bars[SB_FULL + s], last_use[s] & 1) && globaltimer() - t0 < 100000000ull) {
-            }
+            mbar_drain(&bars[SB_FULL + s], last_use[s] & 1, 200000000ll);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
@@ -540,16 +532,13 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
         }
         if (issued) {   // every issued MMA has finished before TMEM is released
             mma_commit(&bars[SB_DRAIN]);
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(&bars[SB_DRAIN], 0) && globaltimer() - t0 < 1000000000ull) {
-            }
+            mbar_drain(&bars[SB_DRAIN], 0, 2000000000ll);
         }
     } else if (warp >= 2) {
         // ---------------- Y builders (warps 2-7); warps 4-7 also flush TMEM ----------------
         const int t = threadIdx.x - 64;          // 0..191
         const int xchunks = p.nkb * kStatRows * 2;
         const uint32_t plane = (uint32_t)p.nkb * blk;
-        const int D16 = p.nkb * 16;
         int gs = 0;
         bool ok = true;
         for (int ui = 0; ok && ui < cu.y; ++ui) {
@@ -595,23 +584,23 @@ bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant
                 break;
             }
             tc_fence_after();
+            // slot columns follow the TMEM columns: [S1 | S2hi | S2lo] blocks of
+            // D16, then S0 (the first ones column), so the flush is a copy; two
+            // 32-column TMEM loads are in flight at a time
             for (int c = 0; c < nchunk; ++c) {
                 const int k = kc0 + c * 128 + q * 32 + lane;
                 float *dst = p.part + (size_t)u.slot * p.Kp * p.P + k;
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * p.ny);
-                for (int n0 = 0; n0 < p.ny; n0 += 32) {
-                    float v[32];
-                    tmem_ld32(ta + n0, v);
+                for (int n0 = 0; n0 < p.P; n0 += 64) {
+                    uint32_t va[32], vb[32];
+                    tmem_ld32_issue(ta + n0, va);
+                    tmem_ld32_issue(ta + n0 + 32, vb);
+                    tmem_ld_wait(va);
+                    tmem_ld_wait(vb);
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
-                        const int n = n0 + e;
-                        if (n >= p.ny) continue;
-                        const int part = n / D16, d = n - part * D16;
-                        if (part < 3) {
-                            if (d < p.D) dst[(size_t)(part * p.D + d) * p.Kp] = v[e];
-                        } else if (d == 0) {
-                            dst[(size_t)(3 * p.D) * p.Kp] = v[e];
-                        }
+                        if (n0 + e < p.P) dst[(size_t)(n0 + e) * p.Kp] = __uint_as_float(va[e]);
+                        if (n0 + 32 + e < p.P) dst[(size_t)(n0 + 32 + e) * p.Kp] = __uint_as_float(vb[e]);
                     }
                 }
             }

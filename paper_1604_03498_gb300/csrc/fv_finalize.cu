@@ -67,14 +67,15 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
     if (d < D && k < K && fr.n > 0) {
         const float *ps = part + (size_t)fr.slot0 * sstride + k;
         const float S0 = slot_sum(ps + (size_t)(P - 1) * Kp, sstride, fr.nslots);
+        const int jb = RAW ? (P - 1) / 3 : D;   // statistic block width (D16 for BF16 slots)
         const float s1 = slot_sum(ps + (size_t)d * Kp, sstride, fr.nslots);
-        const float s2 = slot_sum(ps + (size_t)(D + d) * Kp, sstride, fr.nslots);
+        const float s2 = slot_sum(ps + (size_t)(jb + d) * Kp, sstride, fr.nslots);
         const float inv_n = 1.0f / (float)fr.n;
         const float al = g.alpha[k] * inv_n, be = g.beta[k] * inv_n;
         const float isd = g.s_t[(size_t)d * Kp + k], pr = g.prec_t[(size_t)d * Kp + k];
         float u, v;
         if (RAW) {
-            const float s3 = slot_sum(ps + (size_t)(2 * D + d) * Kp, sstride, fr.nslots);
+            const float s3 = slot_sum(ps + (size_t)(2 * jb + d) * Kp, sstride, fr.nslots);
             const float m = g.mu_t[(size_t)d * Kp + k];
             const float a = fmaf(-m, S0, s1);
             const float b = fmaf(-m, s1, s2) + s3;

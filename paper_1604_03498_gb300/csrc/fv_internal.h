@@ -107,7 +107,8 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 // Statistics slots are component-fastest: part[slot][j][Kp], j < P.
 // Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,
 // L2. raw_moments selects the BF16 form's [S1, S2hi, S2lo, S0] layout
-// (P = 3D+1) over the FP32 form's centred [A, B, S0] layout (P = 2D+1).
+// (blocks of D16 = D rounded up to 16, P = 3*D16+1) over the FP32 form's
+// centred [A, B, S0] layout (blocks of D, P = 2D+1).
 // sq needs B * (Kp / 32) * ceil(D / 8) doubles.
 // err (nullable): device error word of the call; when a kernel set it, every
 // output element becomes NaN so a failed encode can never look valid.

@@ -61,22 +61,32 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t pa
     return ok != 0;
 }
 
-// Bounded wait: gives up after `limit_ns` of global time, records kErrTimeout
-// in *err (device memory) and in *abort (shared), and returns false. Once the
-// CTA is aborting every wait returns false at once.
+// Bounded wait: gives up after `limit_cycles` SM clock cycles (4e9, about two
+// seconds at GB300 clocks), records kErrTimeout in *err (device memory) and
+// in *abort (shared), and returns false. Once the CTA is aborting every wait
+// returns false at once. The bound is read from the SM cycle counter, which
+// is cheap to read, so a wait that succeeds late is noticed at once.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, uint32_t *err,
-                                          bool cluster_scope = false, uint64_t limit_ns = 2000000000ull) {
+                                          bool cluster_scope = false, long long limit_cycles = 4000000000ll) {
     if (*abort) return false;
     if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
+    const long long t0 = clock64();
     while (true) {
         if (cluster_scope ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (globaltimer() - t0 > limit_ns) {
+        if (clock64() - t0 > limit_cycles) {
             *abort = 1u;
             atomicOr(err, kErrTimeout);
             return false;
         }
+    }
+}
+
+// Bounded wait that ignores the abort flag (draining copies or MMAs still in
+// flight before the CTA releases its resources).
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, long long limit_cycles) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity) && clock64() - t0 < limit_cycles) {
     }
 }
 
