@@ -134,6 +134,65 @@ FV_API int fv_encode_batch(const fv_gmm *gmm, const float *X_packed, const int64
 FV_API int fv_encode_batch_bf16(const fv_gmm *gmm, const uint16_t *X_bf16, int64_t ld_x,
                          const int64_t *offsets, int B, float *fv_out, void *cuda_stream);
 
+/* ---- batched form: one CUDA-graph launch per batch ---------------------------
+ * A plan owns every device buffer a batch of up to max_frames frames and
+ * max_rows descriptors needs (bfloat16 input rows, posteriors, statistics
+ * slots, work lists, output vectors) and a CUDA graph of the whole kernel
+ * sequence (posteriors, statistics, finalise), captured once against those
+ * buffers. The kernels read the batch's row and frame counts from device
+ * memory, so a run uploads one small work list and launches the graph once:
+ * frames of uneven size share the persistent kernels (Algorithm 1 for every
+ * frame; the per-block copies and reduction of Algorithm 3 become per-share
+ * statistics slots reduced per frame). FV_PREC_BF16 handles only.
+ *
+ * The statistics grid is chosen by a measured autotune at creation (when
+ * requested): candidate grids are timed on a synthetic batch of the plan's
+ * capacity, the fastest is kept and written to tune_cache (one line per
+ * GPU model, SM count, K, D and capacity), which later plans read back. */
+typedef struct fv_batch_plan fv_batch_plan;
+
+typedef struct {
+    int max_frames;          /* >= 1 */
+    int64_t max_rows;        /* >= 1: total descriptors of a batch */
+    int autotune;            /* 1: time candidate statistics grids at creation */
+    const char *tune_cache;  /* file of tuned grids (read, then appended); NULL: none */
+} fv_batch_plan_config;
+
+typedef struct {
+    int stat_ctas;           /* statistics CTAs per component group (row shares) */
+    int tuned;               /* 1: chosen by timing now, 2: read from tune_cache, 0: default */
+    double tuned_ms;         /* best candidate's time (ms) when tuned now */
+    int64_t max_rows;
+    int max_frames;
+    int ld_x;                /* row pitch (elements) of the plan's input buffer */
+} fv_batch_plan_info;
+
+FV_API int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_config *cfg, fv_batch_plan **out);
+/* Device pointers of the plan's input rows (bfloat16, max_rows x ld_x; write
+ * a batch's descriptors packed back to back, rows D..ld_x-1 ignored) and of
+ * its output (max_frames x 2KD float32). Valid until fv_batch_plan_destroy. */
+FV_API int fv_batch_plan_buffers(fv_batch_plan *plan, uint16_t **x_bf16, float **fv_out);
+/* Copy `rows` bfloat16 descriptor rows (device, row pitch ld_x >= D) into the
+ * plan's input buffer (stream-ordered). */
+FV_API int fv_batch_plan_load_bf16(fv_batch_plan *plan, const uint16_t *X_bf16, int64_t ld_x, int64_t rows,
+                                   void *cuda_stream);
+/* Encode B frames (offsets: B+1 host int64, offsets[0] == 0, offsets[B] <=
+ * max_rows) already in the plan's input buffer with one graph launch; the
+ * vectors land in the plan's output buffer (rows 0..B-1) and, when fv_out is
+ * not NULL, are copied to fv_out (B x 2KD, host or device per out_on_device;
+ * a host copy waits for the result). Ordered on cuda_stream. A plan must not
+ * run on two streams at once. Errors: FV_ERR_INVALID, FV_ERR_EMPTY (every
+ * frame empty; zero vectors), FV_ERR_DEVICE (host output only: a kernel gave
+ * up on a bounded wait), FV_ERR_CUDA. */
+FV_API int fv_batch_plan_run(fv_batch_plan *plan, const int64_t *offsets, int B, float *fv_out, int out_on_device,
+                             void *cuda_stream);
+/* Convert B frames of FP32 descriptors (device, packed N x D rows) into the
+ * plan's input buffer, then run as fv_batch_plan_run. */
+FV_API int fv_batch_plan_run_f32(fv_batch_plan *plan, const float *X, const int64_t *offsets, int B, float *fv_out,
+                                 int out_on_device, void *cuda_stream);
+FV_API int fv_batch_plan_get_info(const fv_batch_plan *plan, fv_batch_plan_info *info);
+FV_API void fv_batch_plan_destroy(fv_batch_plan *plan);
+
 /* Allocation-free variant of fv_encode (plain FP32 form, one descriptor set).
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory, e.g. an application whose own allocator already

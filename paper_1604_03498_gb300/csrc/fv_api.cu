@@ -138,6 +138,19 @@ struct Plan {
 // Split the packed rows into G near-equal shares (boundaries on 64-row
 // multiples) and cut each share at frame boundaries: every piece is a unit
 // with its own slot. A frame's units come out consecutive, in row order.
+void make_plan_balanced(const int64_t *offsets, int B, int G, Plan &p);
+}  // namespace
+
+void build_balanced_plan(const int64_t *offsets, int B, int G, std::vector<FrameInfo> &frames,
+                         std::vector<StatUnit> &units, std::vector<int2> &cta) {
+    Plan p;
+    make_plan_balanced(offsets, B, G, p);
+    frames.swap(p.frames);
+    units.swap(p.units);
+    cta.swap(p.cta);
+}
+
+namespace {
 void make_plan_balanced(const int64_t *offsets, int B, int G, Plan &p) {
     p.frames.resize(B);
     p.units.clear();
@@ -400,6 +413,11 @@ KernelTimer::KernelTimer(const char *name, cudaStream_t st) : slot_(-1), st_(st)
     g_launches.fetch_add(1, std::memory_order_relaxed);
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;   // no event timing inside a graph capture
+    }
     ProfRec r;
     r.name = name;
     if (!g_prof_free.empty()) {
@@ -465,3 +483,7 @@ extern "C" int fv_prof_collect(fv_kernel_stat *out, int max, int *n_out) {
 }
 
 extern "C" int64_t fv_launch_count(void) { return fv::g_launches.load(); }
+
+namespace fv {
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace fv

@@ -81,6 +81,7 @@ __device__ __forceinline__ void square_split(const uint4 &x, uint4 &hi, uint4 &l
 struct PostArgs {
     int64_t rows;
     int ntiles;
+    const int64_t *rows_dev;   // if set, the row count is read here at kernel start (graph replays)
     int nkb;        // D16 / 16
     int Kp;
     int ncta;       // components per CTA (multiple of 16, <= 256)
@@ -139,6 +140,8 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
     }
     const uint32_t rank = p.split > 1 ? cluster_ctarank() : 0u;
     const int cluster_id = blockIdx.x / p.split, nclusters = gridDim.x / p.split;
+    const int64_t nrows = p.rows_dev ? *p.rows_dev : p.rows;
+    const int ntiles = p.rows_dev ? (int)((nrows + kTileRows - 1) / kTileRows) : p.ntiles;
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[PB_BFULL], 1);
@@ -180,7 +183,7 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
                             t * p.Kp + (int)rank * p.ncta);
         int last_use[2] = {-1, -1};
         int i = 0;
-        for (int tile = cluster_id; tile < p.ntiles; tile += nclusters, ++i) {
+        for (int tile = cluster_id; tile < ntiles; tile += nclusters, ++i) {
             const int s = i % p.nstage, u = i / p.nstage;
             if (u > 0 && !mbar_wait(&bars[PB_AEMPTY + s], (u - 1) & 1, abort_flag, p.err)) break;
             uint8_t *ax = smem + L.a + s * L.a_stage;
@@ -202,7 +205,7 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
         bool ok = mbar_wait(&bars[PB_BFULL], 0, abort_flag, p.err);
         int i = 0;
         bool issued = false;
-        for (int tile = cluster_id; ok && tile < p.ntiles; tile += nclusters, ++i) {
+        for (int tile = cluster_id; ok && tile < ntiles; tile += nclusters, ++i) {
             const int s = i % p.nstage, b = i & 1;
             if (!mbar_wait(&bars[PB_AFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
             if (i >= 2 && !mbar_wait(&bars[PB_LEMPTY + b], ((i >> 1) - 1) & 1, abort_flag, p.err)) break;
@@ -239,7 +242,7 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
         const int t = threadIdx.x - 64;
         const int chunks = p.nkb * kTileRows * 2;   // 16-byte chunks of the x blocks
         int i = 0;
-        for (int tile = cluster_id; tile < p.ntiles; tile += nclusters, ++i) {
+        for (int tile = cluster_id; tile < ntiles; tile += nclusters, ++i) {
             const int s = i % p.nstage;
             if (!mbar_wait(&bars[PB_XFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
             uint8_t *sa = smem + L.a + s * L.a_stage;
@@ -272,7 +275,7 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
         float2 *xbuf = reinterpret_cast<float2 *>(smem + L.xchg);
         const float *cl = p.cl2 + rank * p.ncta;
         int i = 0;
-        for (int tile = cluster_id; tile < p.ntiles; tile += nclusters, ++i) {
+        for (int tile = cluster_id; tile < ntiles; tile += nclusters, ++i) {
             const int b = i & 1;
             if (!__all_sync(0xffffffffu, mbar_wait(&bars[PB_LFULL + b], (i >> 1) & 1, abort_flag, p.err))) break;
             tc_fence_after();
@@ -369,7 +372,7 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
                 uint32_t(&nxt)[32] = (cc & 1) ? ra : rb;
                 if (cc + 1 < nh) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
                 const float sc = ex2_approx(mc[cc] - Mref) * inv;
-                if (row < p.rows) {   // 64 bytes of the row: two full 32-byte sectors
+                if (row < nrows) {   // 64 bytes of the row: two full 32-byte sectors
                     uint32_t pk[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k)
@@ -712,7 +715,7 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
 
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
                      const StatUnit *units, const int2 *cta_units, int n_ctas, float *part, int P, int sms,
-                     uint32_t *err, cudaStream_t st) {
+                     uint32_t *err, cudaStream_t st, const int64_t *rows_dev) {
     if (rows <= 0 || n_ctas <= 0) return FV_OK;
     if (get_encoder() != cudaSuccess) return fail(FV_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
     BfCfg c;
@@ -731,6 +734,7 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     PostArgs pa;
     pa.rows = rows;
     pa.ntiles = (int)((rows + kTileRows - 1) / kTileRows);
+    pa.rows_dev = rows_dev;   // rows is then the buffers' capacity
     pa.nkb = nkb;
     pa.Kp = g->Kp;
     pa.ncta = c.ncta;
@@ -743,7 +747,7 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     cudaError_t e = cudaFuncSetAttribute(bf16_posteriors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)c.post_smem);
     if (e != cudaSuccess) return cuda_fail(e, "bf16 posteriors: smem attribute");
-    const int nclusters = std::max(1, std::min(pa.ntiles, sms / c.split));
+    const int nclusters = rows_dev ? std::max(1, sms / c.split) : std::max(1, std::min(pa.ntiles, sms / c.split));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)(nclusters * c.split));

@@ -15,8 +15,10 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
 // err: device word a kernel sets when a bounded wait gives up (zeroed by the caller).
 // units: row segments (one frame each) grouped per statistics CTA;
 // cta_units[c] = (first unit, count) of CTA c.
+// rows_dev (nullable): device row count read by the kernels at start; rows is
+// then the capacity of Xb/gamma (graph replays with a varying row count).
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
                      const StatUnit *units, const int2 *cta_units, int n_ctas, float *part, int P, int sms,
-                     uint32_t *err, cudaStream_t st);
+                     uint32_t *err, cudaStream_t st, const int64_t *rows_dev = nullptr);
 
 }  // namespace fv

@@ -10,7 +10,7 @@
 // forms u and v, takes sign(z) sqrt|z|, and the block writes its [32][8]
 // tiles through shared memory (runs of 8 contiguous floats); the block's sum
 // of squares goes to sq. Kernel B: one block per frame sums the block squares
-// (in FP64, fixed order) and scales the frame's vector by 1/||z||.
+// (fixed-order tree) and scales the frame's vector by 1/||z||.
 //
 // All per-element arithmetic is FP32 (GB300's FP64 rate is a small fraction
 // of its FP32 rate). The BF16 form's raw moments are centred with FMAs whose
@@ -51,10 +51,11 @@ __device__ __forceinline__ float slot_sum(const float *p, size_t stride, int n) 
 template <bool RAW>
 __global__ void __launch_bounds__(FA_THREADS)
 finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, const FrameInfo *__restrict__ frames,
-                  GmmDev g, double *__restrict__ sq, float *__restrict__ out) {
+                  GmmDev g, double *__restrict__ sq, float *__restrict__ out, const int *__restrict__ B_dev) {
     __shared__ float tile[2][32][9];   // [u|v][component][dimension]
     __shared__ float red[FA_THREADS];
     const int f = blockIdx.z;
+    if (B_dev && f >= *B_dev) return;   // graph replay with fewer frames than the grid
     const int k0 = blockIdx.x * 32, d0 = blockIdx.y * 8;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int k = k0 + lane, d = d0 + grp;
@@ -111,46 +112,64 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
 
 __global__ void __launch_bounds__(FB_THREADS)
 finalize_b_kernel(int K, int D, int nb, const double *__restrict__ sq, float *__restrict__ out,
-                  const uint32_t *__restrict__ err) {
-    __shared__ double tot_s;
+                  const uint32_t *__restrict__ err, const int *__restrict__ B_dev) {
+    __shared__ float red[FB_THREADS];
     const int f = blockIdx.x;
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int b = 0; b < nb; ++b) t += sq[(size_t)f * nb + b];
-        tot_s = t;
-    }
+    if (B_dev && f >= *B_dev) return;
+    // fixed-order FP32 tree over the frame's block sums (no FP64 on the hot path)
+    float t = 0.f;
+    for (int b = threadIdx.x; b < nb; b += FB_THREADS) t += (float)sq[(size_t)f * nb + b];
+    red[threadIdx.x] = t;
     __syncthreads();
-    const double tot = tot_s;
+    for (int s = FB_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const float tot = red[0];
     const size_t n = (size_t)2 * K * D;
     float *o = out + (size_t)f * n;
     if (err && *err) {   // an earlier kernel of this call gave up: poison the output
         for (size_t j = threadIdx.x; j < n; j += FB_THREADS) o[j] = __int_as_float(0x7fc00000);
         return;
     }
-    if (!(tot > 0.0)) return;   // all-zero vector stays zero
-    const float inv = (float)(1.0 / sqrt(tot));
-    for (size_t j = threadIdx.x; j < n; j += FB_THREADS) o[j] *= inv;
+    if (!(tot > 0.f)) return;   // all-zero vector stays zero
+    const float inv = rsqrtf(tot);
+    if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+        float4 *o4 = reinterpret_cast<float4 *>(o);
+        for (size_t j = threadIdx.x; j < n / 4; j += FB_THREADS) {
+            float4 v = o4[j];
+            v.x *= inv;
+            v.y *= inv;
+            v.z *= inv;
+            v.w *= inv;
+            o4[j] = v;
+        }
+    } else {
+        for (size_t j = threadIdx.x; j < n; j += FB_THREADS) o[j] *= inv;
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments, const FrameInfo *frames,
-                            int B, double *sq, float *out, cudaStream_t st, const uint32_t *err) {
+                            int B, double *sq, float *out, cudaStream_t st, const uint32_t *err, const int *B_dev) {
     if (B <= 0) return cudaSuccess;
     const int nbx = g->Kp / 32, nby = (g->D + 7) / 8, nb = nbx * nby;
     dim3 grid_a((unsigned)nbx, (unsigned)nby, (unsigned)B);
     if (raw_moments) {
         KernelTimer kt_("finalize_a", st);
-        finalize_a_kernel<true><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out);
+        finalize_a_kernel<true><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out,
+                                                                B_dev);
     } else {
         KernelTimer kt_("finalize_a", st);
-        finalize_a_kernel<false><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out);
+        finalize_a_kernel<false><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out,
+                                                                 B_dev);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     {
         KernelTimer kt_("finalize_b", st);
-        finalize_b_kernel<<<(unsigned)B, FB_THREADS, 0, st>>>(g->K, g->D, nb, sq, out, err);
+        finalize_b_kernel<<<(unsigned)B, FB_THREADS, 0, st>>>(g->K, g->D, nb, sq, out, err, B_dev);
     }
     return cudaGetLastError();
 }

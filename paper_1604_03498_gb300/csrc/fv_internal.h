@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fv.h"
 
@@ -34,6 +35,9 @@ class KernelTimer {
     int slot_;
     cudaStream_t st_;
 };
+
+// Adds kernel launches made by a graph replay to the launch counter.
+void count_launches(int n);
 
 // ---- limits ----------------------------------------------------------------
 constexpr int kMaxK_F32 = 512;    // posteriors keep a BM x Kp row block in shared memory
@@ -96,6 +100,11 @@ struct StatUnit {
     int32_t slot;    // statistics slot written by this range
 };
 
+// Balanced work plan of the BF16 statistics (see fv_api.cu): G row shares,
+// cut at frame boundaries into units; cta[c] = (first unit, count).
+void build_balanced_plan(const int64_t *offsets, int B, int G, std::vector<FrameInfo> &frames,
+                         std::vector<StatUnit> &units, std::vector<int2> &cta);
+
 // ---- kernels' host launchers --------------------------------------------------
 cudaError_t launch_prep(const fv_gmm *g, const float *w, const float *mu, const float *var, cudaStream_t st);
 
@@ -114,6 +123,6 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 // output element becomes NaN so a failed encode can never look valid.
 cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments,
                             const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
-                            const uint32_t *err = nullptr);
+                            const uint32_t *err = nullptr, const int *B_dev = nullptr);
 
 }  // namespace fv

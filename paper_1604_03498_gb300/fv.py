@@ -48,6 +48,16 @@ class fv_gmm_desc(ctypes.Structure):
                 ("means", ctypes.c_void_p), ("variances", ctypes.c_void_p)]
 
 
+class fv_batch_plan_config(ctypes.Structure):
+    _fields_ = [("max_frames", ctypes.c_int), ("max_rows", ctypes.c_int64), ("autotune", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
+
+
+class fv_batch_plan_info(ctypes.Structure):
+    _fields_ = [("stat_ctas", ctypes.c_int), ("tuned", ctypes.c_int), ("tuned_ms", ctypes.c_double),
+                ("max_rows", ctypes.c_int64), ("max_frames", ctypes.c_int), ("ld_x", ctypes.c_int)]
+
+
 def lib():
     """Load (building first if needed) the CUDA library. Raises on failure."""
     global _lib
@@ -72,6 +82,20 @@ def lib():
             L.fv_encode_batch_bf16.restype = I
             L.fv_last_error.argtypes = []
             L.fv_last_error.restype = ctypes.c_char_p
+            L.fv_batch_plan_create.argtypes = [P, ctypes.POINTER(fv_batch_plan_config), ctypes.POINTER(P)]
+            L.fv_batch_plan_create.restype = I
+            L.fv_batch_plan_load_bf16.argtypes = [P, P, I64, I64, P]
+            L.fv_batch_plan_load_bf16.restype = I
+            L.fv_batch_plan_run.argtypes = [P, P, I, P, I, P]
+            L.fv_batch_plan_run.restype = I
+            L.fv_batch_plan_run_f32.argtypes = [P, P, P, I, P, I, P]
+            L.fv_batch_plan_run_f32.restype = I
+            L.fv_batch_plan_get_info.argtypes = [P, ctypes.POINTER(fv_batch_plan_info)]
+            L.fv_batch_plan_get_info.restype = I
+            L.fv_batch_plan_buffers.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P)]
+            L.fv_batch_plan_buffers.restype = I
+            L.fv_batch_plan_destroy.argtypes = [P]
+            L.fv_batch_plan_destroy.restype = None
             L.fv_encode_noalloc.argtypes = [P, P, I64, P, P]
             L.fv_encode_noalloc.restype = I
             L.fv_prof_enable.argtypes = [I]
@@ -208,6 +232,61 @@ def fv_encode_noalloc(g: Gmm, X, out, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) 
     xp, _ = _ptr(X)
     op, _ = _ptr(out)
     return _check(lib().fv_encode_noalloc(g.handle, xp, int(X.shape[0]), op, _stream(stream)), allow)
+
+
+class BatchPlan:
+    """Owns an fv_batch_plan (the batched form: one CUDA-graph launch per batch)."""
+
+    def __init__(self, handle, K, D):
+        self.handle = handle
+        self.K, self.D = K, D
+
+    def close(self):
+        if self.handle:
+            lib().fv_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fv_batch_plan_create(g: Gmm, max_frames: int, max_rows: int, autotune: bool = False,
+                         tune_cache: str | None = None) -> BatchPlan:
+    cfg = fv_batch_plan_config(int(max_frames), int(max_rows), int(bool(autotune)),
+                               tune_cache.encode() if tune_cache else None)
+    h = ctypes.c_void_p()
+    _check(lib().fv_batch_plan_create(g.handle, ctypes.byref(cfg), ctypes.byref(h)))
+    return BatchPlan(h, g.K, g.D)
+
+
+def fv_batch_plan_get_info(p: BatchPlan) -> dict:
+    info = fv_batch_plan_info()
+    _check(lib().fv_batch_plan_get_info(p.handle, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in fv_batch_plan_info._fields_}
+
+
+def fv_batch_plan_load_bf16(p: BatchPlan, X_bf16, ld_x: int, rows: int, stream=None) -> int:
+    xp, _ = _ptr(X_bf16)
+    return _check(lib().fv_batch_plan_load_bf16(p.handle, xp, int(ld_x), int(rows), _stream(stream)))
+
+
+def fv_batch_plan_run(p: BatchPlan, offsets, out=None, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    """C fv_batch_plan_run: encode the batch already in the plan's input buffer;
+    out (B x 2KD, host or device) receives a copy of the vectors when given."""
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    op, od = _ptr(out)
+    return _check(lib().fv_batch_plan_run(p.handle, offs.ctypes.data, offs.size - 1, op, od, _stream(stream)), allow)
+
+
+def fv_batch_plan_run_f32(p: BatchPlan, X, offsets, out=None, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    xp, _ = _ptr(X)
+    op, od = _ptr(out)
+    return _check(lib().fv_batch_plan_run_f32(p.handle, xp, offs.ctypes.data, offs.size - 1, op, od,
+                                              _stream(stream)), allow)
 
 
 class fv_kernel_stat(ctypes.Structure):
