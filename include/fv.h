@@ -193,6 +193,54 @@ FV_API int fv_batch_plan_run_f32(fv_batch_plan *plan, const float *X, const int6
 FV_API int fv_batch_plan_get_info(const fv_batch_plan *plan, fv_batch_plan_info *info);
 FV_API void fv_batch_plan_destroy(fv_batch_plan *plan);
 
+/* ---- serving form: continuous batching of frames from many streams --------
+ * A server keeps the GMM and two batch plans resident on the device. Client
+ * threads submit frames (host FP32 descriptors) as they arrive; a frame is
+ * admitted only while the device memory of admitted, unfinished frames stays
+ * within hbm_budget_bytes and fewer than max_slots frames are in flight,
+ * otherwise submit answers FV_ERR_BUSY at once. A scheduler thread gathers
+ * the admitted frames into the next batch while the previous batch runs on
+ * the GPU (two plans on two streams alternate), so frames that arrive while
+ * others are being encoded join the next batch instead of waiting for a
+ * queue to drain. Every frame is encoded exactly as fv_encode_batch would
+ * encode it (a frame's vector does not depend on the other frames of its
+ * batch beyond rounding of the per-share partial sums).
+ * FV_PREC_BF16 handles only. */
+typedef struct {
+    int max_slots;                   /* frames admitted and not yet polled */
+    int64_t hbm_budget_bytes;        /* device bytes for admitted frames' descriptors */
+    int64_t max_batch_descriptors;   /* capacity of one GPU batch (rows) */
+    int max_batch_frames;            /* capacity of one GPU batch (frames) */
+    int64_t max_frame_descriptors;   /* largest accepted frame */
+    int64_t batch_window_ns;         /* a batch that is not full waits at most this long
+                                        after its oldest frame's submit (0: launch at once) */
+} fv_server_config;
+
+typedef struct {
+    int status;             /* FV_OK, or the error of the frame's batch */
+    int stream_id;
+    int64_t n;              /* descriptors */
+    int64_t latency_ns;     /* submit -> result ready on the host */
+    int64_t queue_ns;       /* submit -> its batch launched */
+    int batch_frames;       /* frames in the batch that encoded it */
+} fv_result_info;
+
+FV_API int fv_server_create(const fv_gmm *gmm, const fv_server_config *cfg, fv_server **out);
+/* Copy a frame (X: host float32 N x D, 1 <= N <= max_frame_descriptors) into
+ * the server; returns when X may be reused. *ticket identifies the result.
+ * Errors: FV_ERR_BUSY (budget or slots exhausted: retry later),
+ * FV_ERR_INVALID, FV_ERR_CUDA. */
+FV_API int fv_server_submit(fv_server *srv, int stream_id, const float *X, int64_t N, uint64_t *ticket);
+/* Wait up to timeout_ns (0: do not wait, < 0: wait without limit) for a
+ * ticket's result; on FV_OK writes the 2KD vector to fv_out (host) and info,
+ * and releases the ticket. FV_PENDING when not ready, FV_ERR_NOTFOUND for an
+ * unknown or already released ticket, FV_ERR_TIMEOUT when the wait expired. */
+FV_API int fv_server_poll(fv_server *srv, uint64_t ticket, float *fv_out, fv_result_info *info, int64_t timeout_ns);
+/* Counters: admitted, refused (busy), completed frames, batches launched. */
+FV_API int fv_server_stats(const fv_server *srv, int64_t *admitted, int64_t *refused, int64_t *completed,
+                           int64_t *batches);
+FV_API void fv_server_destroy(fv_server *srv);
+
 /* Allocation-free variant of fv_encode (plain FP32 form, one descriptor set).
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory, e.g. an application whose own allocator already

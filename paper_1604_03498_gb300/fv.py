@@ -58,6 +58,17 @@ class fv_batch_plan_info(ctypes.Structure):
                 ("max_rows", ctypes.c_int64), ("max_frames", ctypes.c_int), ("ld_x", ctypes.c_int)]
 
 
+class fv_server_config(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64),
+                ("max_batch_descriptors", ctypes.c_int64), ("max_batch_frames", ctypes.c_int),
+                ("max_frame_descriptors", ctypes.c_int64), ("batch_window_ns", ctypes.c_int64)]
+
+
+class fv_result_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("stream_id", ctypes.c_int), ("n", ctypes.c_int64),
+                ("latency_ns", ctypes.c_int64), ("queue_ns", ctypes.c_int64), ("batch_frames", ctypes.c_int)]
+
+
 def lib():
     """Load (building first if needed) the CUDA library. Raises on failure."""
     global _lib
@@ -96,6 +107,16 @@ def lib():
             L.fv_batch_plan_buffers.restype = I
             L.fv_batch_plan_destroy.argtypes = [P]
             L.fv_batch_plan_destroy.restype = None
+            L.fv_server_create.argtypes = [P, ctypes.POINTER(fv_server_config), ctypes.POINTER(P)]
+            L.fv_server_create.restype = I
+            L.fv_server_submit.argtypes = [P, I, P, I64, ctypes.POINTER(ctypes.c_uint64)]
+            L.fv_server_submit.restype = I
+            L.fv_server_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(fv_result_info), I64]
+            L.fv_server_poll.restype = I
+            L.fv_server_stats.argtypes = [P] + [ctypes.POINTER(I64)] * 4
+            L.fv_server_stats.restype = I
+            L.fv_server_destroy.argtypes = [P]
+            L.fv_server_destroy.restype = None
             L.fv_encode_noalloc.argtypes = [P, P, I64, P, P]
             L.fv_encode_noalloc.restype = I
             L.fv_prof_enable.argtypes = [I]
@@ -287,6 +308,60 @@ def fv_batch_plan_run_f32(p: BatchPlan, X, offsets, out=None, stream=None, allow
     op, od = _ptr(out)
     return _check(lib().fv_batch_plan_run_f32(p.handle, xp, offs.ctypes.data, offs.size - 1, op, od,
                                               _stream(stream)), allow)
+
+
+class Server:
+    """Owns an fv_server (the serving form: continuous batching)."""
+
+    def __init__(self, handle, K, D):
+        self.handle = handle
+        self.K, self.D = K, D
+
+    def close(self):
+        if self.handle:
+            lib().fv_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fv_server_create(g: Gmm, max_slots: int, hbm_budget_bytes: int, max_batch_descriptors: int,
+                     max_batch_frames: int, max_frame_descriptors: int, batch_window_ns: int = 0) -> Server:
+    cfg = fv_server_config(int(max_slots), int(hbm_budget_bytes), int(max_batch_descriptors), int(max_batch_frames),
+                           int(max_frame_descriptors), int(batch_window_ns))
+    h = ctypes.c_void_p()
+    _check(lib().fv_server_create(g.handle, ctypes.byref(cfg), ctypes.byref(h)))
+    return Server(h, g.K, g.D)
+
+
+def fv_server_submit(s: Server, stream_id: int, X, allow=(FV_OK,)):
+    """C fv_server_submit with host descriptors X (N x D float32).
+    Returns (status, ticket)."""
+    xp, xd = _ptr(X)
+    if xd:
+        raise ValueError("fv_server_submit takes host descriptors")
+    t = ctypes.c_uint64()
+    st = _check(lib().fv_server_submit(s.handle, int(stream_id), xp, int(X.shape[0]), ctypes.byref(t)), allow)
+    return st, t.value
+
+
+def fv_server_poll(s: Server, ticket: int, out=None, timeout_ns: int = -1,
+                   allow=(FV_OK, FV_PENDING, FV_ERR_TIMEOUT)):
+    """C fv_server_poll; out is a host float32 array of 2KD. Returns (status, info dict)."""
+    op, _ = _ptr(out)
+    info = fv_result_info()
+    st = _check(lib().fv_server_poll(s.handle, ctypes.c_uint64(ticket), op, ctypes.byref(info), int(timeout_ns)), allow)
+    return st, {f: getattr(info, f) for f, _ in fv_result_info._fields_}
+
+
+def fv_server_stats(s: Server) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().fv_server_stats(s.handle, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("admitted", "refused", "completed", "batches"), (x.value for x in v)))
 
 
 class fv_kernel_stat(ctypes.Structure):
