@@ -310,6 +310,144 @@ def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, stream, barrier, dist,
     return r
 
 
+def serving_form(args):
+    """Serving workload: 64 simulated video streams at 30 fps with Poisson
+    jitter (exponential, mean 5 ms, clipped to the frame period), per-frame N
+    ~ Uniform{8000..40000}, D=64, K=512 GMM resident on the device, admission
+    by a 16 GB HBM budget, bf16 operands. The trace is replayed in real time
+    through the server (submit from one client thread, results collected by a
+    second) and, on the same trace, through the plain FP32 per-frame loop
+    (fv_encode with host buffers, one frame at a time). A closed-loop run of
+    each then gives the sustainable throughput. Frame contents are prefixes
+    of a 32-frame pool of GMM-sampled descriptors (80% GMM, 20% outliers)."""
+    import torch
+    from paper_1604_03498_gb300 import fv
+    K, D, NS, FPS = 512, 64, 64, 30.0
+    w, mu, var = synth.make_gmm(K, D, seed=1)
+    pool = [synth.sample_descriptors(w, mu, var, 40000, seed=90_000 + i, gmm_frac=0.8) for i in range(32)]
+    pool_t = [torch.from_numpy(p).pin_memory() for p in pool]    # pinned host frames (kept alive here)
+    pool_h = [t.numpy() for t in pool_t]
+    arr = synth.arrival_times(NS, FPS, args.serve_seconds, 0.005, seed=5)
+    sizes = synth.frame_sizes(len(arr), 8000, 40000, seed=5)
+    frames = [pool_h[(int(s) * 7 + int(f)) % 32][:int(n)] for (t, s, f), n in zip(arr, sizes)]
+    total_desc = int(sizes.sum())
+    gbf = fv.fv_gmm_load(w, mu, var, fv.FV_PREC_BF16)
+    g32 = fv.fv_gmm_load(w, mu, var, fv.FV_PREC_FP32)
+    srv = fv.fv_server_create(gbf, max_slots=4096, hbm_budget_bytes=16 << 30, max_batch_descriptors=2_000_000,
+                              max_batch_frames=128, max_frame_descriptors=40000, batch_window_ns=0)
+    fvlen = 2 * K * D
+
+    def replay_server(paced):
+        import threading
+        tickets, lat, qd, bsz = [], [], [], []
+        done_evt = threading.Event()
+        order = []
+        lock = threading.Lock()
+        retries = [0]
+
+        def poller():
+            out = np.zeros(fvlen, np.float32)
+            i = 0
+            while True:
+                with lock:
+                    if i < len(order):
+                        t = order[i]
+                    elif done_evt.is_set():
+                        break
+                    else:
+                        t = None
+                if t is None:
+                    time.sleep(0.0002)
+                    continue
+                st, info = fv.fv_server_poll(srv, t, out, timeout_ns=60_000_000_000)
+                lat.append(info["latency_ns"] / 1e6)
+                qd.append(info["queue_ns"] / 1e6)
+                bsz.append(info["batch_frames"])
+                i += 1
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for (ta, s, f), X in zip(arr, frames):
+            if paced:
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            while True:
+                st, t = fv.fv_server_submit(srv, int(s), X, allow=(fv.FV_OK, fv.FV_ERR_BUSY))
+                if st == fv.FV_OK:
+                    break
+                retries[0] += 1
+                time.sleep(0.0001)
+            with lock:
+                order.append(t)
+        done_evt.set()
+        th.join()
+        wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        return {"frames": len(frames), "descriptors": total_desc, "wall_s": wall,
+                "descriptors_per_s": total_desc / wall, "frames_per_s": len(frames) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "queue_p50_ms": float(np.percentile(qd, 50)),
+                "batch_frames_mean": float(np.mean(bsz)), "batch_frames_max": int(np.max(bsz)),
+                "busy_retries": retries[0]}
+
+    def replay_fp32(paced, limit=None):
+        out = np.zeros(fvlen, np.float32)
+        lat = []
+        t0 = time.perf_counter()
+        n_done, d_done = 0, 0
+        for (ta, s, f), X in zip(arr, frames):
+            if paced:
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            fv.fv_encode(g32, X, out, allow=(fv.FV_OK,))
+            now = time.perf_counter() - t0
+            lat.append((now - (ta if paced else 0.0)) * 1e3)
+            n_done += 1
+            d_done += X.shape[0]
+            if limit and now > limit:
+                break
+        wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        r = {"frames": n_done, "descriptors": d_done, "wall_s": wall, "descriptors_per_s": d_done / wall,
+             "frames_per_s": n_done / wall}
+        if paced:
+            r.update(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                     max_ms=float(lat.max()))
+        return r
+
+    # warm both paths
+    for X in frames[:8]:
+        st, t = fv.fv_server_submit(srv, 0, X)
+        fv.fv_server_poll(srv, t, np.zeros(fvlen, np.float32), timeout_ns=10_000_000_000)
+        fv.fv_encode(g32, X, np.zeros(fvlen, np.float32))
+    served = replay_server(True)
+    plain = replay_fp32(True)
+    served_sat = replay_server(False)
+    plain_sat = replay_fp32(False, limit=max(5.0, args.serve_seconds / 2))
+    stats = fv.fv_server_stats(srv)
+    # parity of a sample of served frames (1 in 100) with the oracle on the same bf16 input
+    import oracle
+    errs = []
+    for j in range(0, min(len(frames), 300), 100):
+        X = frames[j]
+        st, t = fv.fv_server_submit(srv, 0, X)
+        out = np.zeros(fvlen, np.float32)
+        fv.fv_server_poll(srv, t, out, timeout_ns=10_000_000_000)
+        errs.append(float(np.abs(out - oracle.encode(synth.to_bf16_grid(X), w, mu, var)["fv"]).max()))
+    srv.close()
+    gbf.close()
+    g32.close()
+    return {"workload": f"{NS} streams x {FPS:.0f} fps x {args.serve_seconds:.0f} s, N ~ U{{8000..40000}}, "
+                        f"D={D}, K={K}, 16 GB admission budget, bf16",
+            "served_bf16_paced": served, "plain_fp32_paced": plain,
+            "served_bf16_saturated": served_sat, "plain_fp32_saturated": plain_sat,
+            "server_stats": stats, "max_abs_err_vs_oracle_sample": max(errs) if errs else None,
+            "oracle_sample_frames": len(errs)}
+
+
 def ncu_case(kind: str) -> int:
     """A small fixed workload for profiler captures: the same kernels as the
     benchmark, called twice (the first call warms up), a few hundred MB on the
@@ -349,6 +487,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="length of the simulated 64-stream serving trace (the workload's full length is 60)")
     ap.add_argument("--ncu-case", choices=["fp32", "bf16", "bf16_batched"], default=None,
                     help="run a small fixed workload twice and exit (for ncu captures)")
     args = ap.parse_args()
@@ -456,6 +596,10 @@ def main():
         f0 = Xb[0].float().cpu().numpy()
         ref = oracle.encode(f0, w, mu, var)["fv"]
         forms["bf16"]["max_abs_err_vs_oracle_frame0"] = float(np.abs(outb[0].cpu().numpy() - ref).max())
+
+    # ---- serving form: 64 streams x 30 fps, K=512 (rank 0 only: one GPU) ----
+    if rank == 0 and args.serve_seconds > 0:
+        forms["serving"] = serving_form(args)
 
     # ---- end to end through the C ABI with pinned host buffers (FP32 form) ----
     Xh = torch.from_numpy(np.stack(frames)).pin_memory()
