@@ -214,11 +214,8 @@ def timed(step, steps, stream, barrier, dist):
     torch.cuda.synchronize()
     barrier()
     launches = fv.fv_launch_count() - n0
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_1604_03498_gb300.multigpu import reduce_over_ranks
+    ms = reduce_over_ranks(e0.elapsed_time(e1), "max", device="cuda")
     return ms, launches
 
 
@@ -612,11 +609,8 @@ def main():
     for _ in range(e2e_steps):
         for f in range(POOL):
             fv.fv_encode(g32, Xh[f], outh[f], allow=(fv.FV_OK,))
-    dt = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    from paper_1604_03498_gb300.multigpu import reduce_over_ranks
+    dt = reduce_over_ranks(time.perf_counter() - t0, "max", device="cuda")
     e2e = {"value": world * e2e_steps * POOL * N_DESC / dt, "unit": "descriptors/s",
            "h2d_bytes_per_step": POOL * N_DESC * D_DIM * 4, "d2h_bytes_per_step": POOL * 2 * KD * 4,
            "steps": e2e_steps, "form": "fp32, one fv_encode per frame, pinned host input and output"}
