@@ -176,17 +176,18 @@ def run_reference(args):
 
 
 # ---- measured traffic of a kernel (from a committed ncu summary) ------------------
-def measured_traffic(kernel: str, source: str):
-    """DRAM bytes per launch recorded in profiles/traffic.md for `kernel`, valid
-    only while the kernel's source file still has the hash recorded there."""
+def measured_traffic(kernel: str, source: str, workload: str):
+    """DRAM bytes per launch recorded in profiles/traffic.md for `kernel` on
+    `workload` ("frame" or "batch64"), valid only while the kernel's source
+    file still has the hash recorded there."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     src = os.path.join(ROOT, "paper_1604_03498_gb300", "csrc", source)
     if not (os.path.exists(path) and os.path.exists(src)):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
     for ln in open(path):
-        m = re.match(r"\|\s*(\S+)\s*\|\s*(\w+)\s*\|\s*([0-9.eE+]+)\s*\|", ln)
-        if m and m.group(1) == kernel and m.group(2) == sha:
+        m = re.match(r"\|\s*(\S+)\s*\|\s*(\w+)\s*\|\s*([0-9.eE+]+)\s*\|\s*(\w+)\s*\|", ln)
+        if m and m.group(1) == kernel and m.group(2) == sha and m.group(4) == workload:
             return float(m.group(3))
     return None
 
@@ -234,7 +235,7 @@ def kernel_times(step, steps):
     return prof
 
 
-def roofline_of(prof, work, bound, peak, unit, peak_basis, source, issued=None):
+def roofline_of(prof, work, bound, peak, unit, peak_basis, source, issued=None, workload="frame"):
     overall = max(prof.items(), key=lambda kv: kv[1][1])[0]
     cands = [kv for kv in prof.items() if kv[0] in work] or list(prof.items())
     name, (n, ms) = max(cands, key=lambda kv: kv[1][1])
@@ -244,7 +245,8 @@ def roofline_of(prof, work, bound, peak, unit, peak_basis, source, issued=None):
                 "traffic": None, "dominant_kernel": overall}
     achieved = work[name] / per_launch_s / 1e12
     r = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-         "traffic": measured_traffic(name, source), "peak_basis": peak_basis, "launch_ms": per_launch_s * 1e3,
+         "traffic": measured_traffic(name, source, workload), "traffic_workload": workload,
+         "peak_basis": peak_basis, "launch_ms": per_launch_s * 1e3,
          "share": ms / sum(v[1] for v in prof.values()), "dominant_kernel": overall}
     if issued and name in issued:
         r["issued_frac"] = issued[name] / per_launch_s / 1e12 / peak
@@ -545,7 +547,10 @@ def main():
     clk = clocks.stop()
     value = world * args.steps * POOL * N_DESC / (ms / 1e3)
     prof32 = kernel_times(step32, args.steps)
-    roof32 = roofline_of(prof32, {"f32_posteriors": 4.0 * KD * N_DESC, "f32_stats": 6.0 * KD * N_DESC},
+    # algorithmic flops per frame: log-likelihoods 2K(2D) (two FMAs per (k, d)),
+    # statistics 2K(2D+1) (the gamma^T [X, X^2, 1] contraction)
+    roof32 = roofline_of(prof32, {"f32_posteriors": 4.0 * KD * N_DESC,
+                                  "f32_stats": 2.0 * K_COMP * (2 * D_DIM + 1) * N_DESC},
                          "alu", alu_peak, "TFLOP/s", f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                          "fv_fp32.cu")
 
@@ -576,7 +581,8 @@ def main():
         rows_per_launch = N_DESC * frames_per_call
         roof = roofline_of(prof, {k: v * rows_per_launch for k, v in work_bf.items()}, "tensor", tc_peak,
                            "TFLOP/s", "MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)",
-                           "fv_bf16.cu", {k: v * rows_per_launch for k, v in issued_bf.items()})
+                           "fv_bf16.cu", {k: v * rows_per_launch for k, v in issued_bf.items()},
+                           workload="frame" if frames_per_call == 1 else "batch64")
         vb = world * args.steps * POOL * N_DESC / (msb / 1e3)
         forms[name] = {"value": vb, "unit": "descriptors/s", "frames_per_s": vb / N_DESC,
                        "us_per_frame": 1e3 * msb / (args.steps * POOL), "frames_per_call": frames_per_call,
