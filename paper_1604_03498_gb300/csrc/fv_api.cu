@@ -3,10 +3,10 @@
 // kernel sequence of each precision form:
 //
 //   FP32 form: f32 posteriors -> f32 statistics -> finalise
-//   BF16 form: bf16 convert (FP32 input only) -> tcgen05 posteriors ->
-//              tcgen05 statistics -> finalise
+//   BF16 form: bf16 convert (FP32 input only) -> fused tcgen05 encoder
+//              (posteriors and statistics, gamma kept on chip) -> finalise
 //
-// Scratch (posteriors, per-range statistics, the work list, staging copies of
+// Scratch (FP32 posteriors, per-range statistics, the work list, staging copies of
 // host inputs/outputs) comes from cudaMallocAsync on the caller's stream and
 // goes back with cudaFreeAsync on the same stream, so a call neither
 // synchronises the device nor holds memory after its work ends. The pool's
@@ -130,14 +130,15 @@ bool is_device_ptr(const void *p) {
 struct Plan {
     std::vector<FrameInfo> frames;
     std::vector<StatUnit> units;
-    std::vector<int2> cta;   // BF16 statistics: (first unit, count) per persistent CTA
+    std::vector<int2> cta;   // BF16: (first unit, count) per share (one persistent cluster)
     int64_t rows = 0;
     int nonempty = 0;
 };
 
-// Split the packed rows into G near-equal shares (boundaries on 64-row
-// multiples) and cut each share at frame boundaries: every piece is a unit
-// with its own slot. A frame's units come out consecutive, in row order.
+// Split the packed rows into G near-equal shares (boundaries on 128-row
+// multiples, the BF16 kernel's tile) and cut each share at frame boundaries:
+// every piece is a unit with its own slot. A frame's units come out
+// consecutive, in row order.
 void make_plan_balanced(const int64_t *offsets, int B, int G, Plan &p);
 }  // namespace
 
@@ -168,7 +169,7 @@ void make_plan_balanced(const int64_t *offsets, int B, int G, Plan &p) {
     int f = 0;
     int64_t a = 0;
     for (int c = 0; c < G; ++c) {
-        const int64_t e = (c == G - 1) ? R : std::max<int64_t>(a, (R * (c + 1) / G) / 64 * 64);
+        const int64_t e = (c == G - 1) ? R : std::max<int64_t>(a, (R * (c + 1) / G) / 128 * 128);
         const int first = (int)p.units.size();
         while (f < B && offsets[f + 1] <= a) ++f;
         for (int ff = f; ff < B && offsets[ff] < e; ++ff) {
@@ -241,8 +242,8 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
 
     Plan plan;
     if (bf16) {
-        // persistent statistics CTAs over balanced shares of the packed rows
-        make_plan_balanced(offsets, B, bf16_stat_ctas(g, rows, sms), plan);
+        // persistent clusters over balanced shares of the packed rows
+        make_plan_balanced(offsets, B, bf16_shares(g, rows, sms), plan);
     } else {
         // rows per statistics range: aim for about three blocks per SM in one wave
         const int64_t blocks_per_range = (int64_t)(Kp / 64) * ((D + 63) / 64);
@@ -261,7 +262,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     const size_t o_x = (!x_on_device && rows > 0) ? s.take(sizeof(float) * rows * D) : 0;
     const bool need_x_f32_stage = !x_on_device && rows > 0;
     const size_t o_xb = (bf16 && !x_bf16 && rows > 0) ? s.take(sizeof(uint16_t) * rows * ldx_dev) : 0;
-    const size_t o_gam = s.take((bf16 ? sizeof(uint16_t) : sizeof(float)) * std::max<int64_t>(rows, 1) * Kp);
+    const size_t o_gam = !bf16 ? s.take(sizeof(float) * std::max<int64_t>(rows, 1) * Kp) : 0;
     const size_t o_part = s.take(sizeof(float) * std::max(nslots, 1) * (size_t)Kp * P);
     const size_t o_fr = s.take(sizeof(FrameInfo) * B);
     const size_t o_un = s.take(sizeof(StatUnit) * std::max(nslots, 1));
@@ -322,8 +323,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
                 }
                 xb = xconv;
             }
-            uint16_t *gam = (uint16_t *)(s.base + o_gam);
-            rc = run_bf16_encoder(g, xb, ldx_dev, rows, gam, und, ctad, nctas, part, P, sms, errd, st);
+            rc = run_bf16_encoder(g, xb, ldx_dev, rows, und, ctad, nctas, part, P, errd, st);
             if (rc != FV_OK) break;
         }
         if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd)) != cudaSuccess) {

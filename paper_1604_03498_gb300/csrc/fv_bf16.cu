@@ -1,40 +1,53 @@
 // BF16 precision form of the encoder on the 5th-generation tensor cores
-// (tcgen05 MMA with TMEM accumulators, TMA-fed shared-memory operands).
+// (tcgen05 MMA with TMEM accumulators, TMA-fed shared-memory operands), as
+// one fused kernel: the posteriors never leave the SM.
 //
-// Log-likelihood GEMM (the distance/posterior step of Algorithm 1; the
-// paper's Phase 1, Algorithm 2, "the most time consuming computation"):
-//   l_ik = c_k + sum_d x_id Q_kd + sum_d x_id^2 R_kd,
-//   Q = mu/sigma^2, R = -1/(2 sigma^2), c_k = log w_k - 1/2 sum log sigma^2
-//   - 1/2 sum mu^2/sigma^2 (FP64 on the device, once per GMM).
-// x is bfloat16 (exact), Q and R are split into bf16 hi + lo parts, and x^2
-// (16 significant bits for a bf16 x) into hi + lo, so five products
-//   x Q_hi + x Q_lo + x2_hi R_hi + x2_hi R_lo + x2_lo R_hi
-// accumulate in FP32 in TMEM and undo the cancellation between x^2/sigma^2
-// and 2 x mu/sigma^2. A 128-row tile x all components of the CTA lives in one
-// TMEM buffer (two buffers alternate so the next tile's MMAs overlap this
-// tile's epilogue). The epilogue (one thread per row) makes three passes over
-// the row in TMEM: row max, exponentials (stored back into TMEM) with their
-// sum, then normalised posteriors written to global memory as bfloat16.
-// With more than 256 components the components are split over a 2-CTA
-// cluster; the two CTAs exchange each row's (max, sum) through distributed
-// shared memory.
+// Per 128-row tile, each CTA of a cluster owns 128 components and runs
 //
-// Statistics GEMM (Algorithm 1 second loop; Phase 2, Algorithm 3):
-//   [S1 | S2hi | S2lo | S0] = gamma^T [X | X2hi | X2lo | 1]
-// with gamma^T (components x rows) and the row-major Y both read as MN-major
-// operands; 128-component accumulators live in TMEM for a whole row range and
-// are written to that range's statistics slot (the paper's per-block copies).
-// The finalise kernel centres the raw moments in FP64.
+// 1. the log-likelihood GEMM (the distance/posterior step of Algorithm 1;
+//    the paper's Phase 1, Algorithm 2, its most expensive part):
+//      l_ik = c_k + sum_d x_id Q_kd + sum_d x_id^2 R_kd,
+//      Q = mu/sigma^2, R = -1/(2 sigma^2), c_k = log w_k - 1/2 sum log sigma^2
+//      - 1/2 sum mu^2/sigma^2 (FP64 on the device, once per GMM).
+//    x is bfloat16 (exact), Q and R are split into bf16 hi + lo parts, and
+//    x^2 (16 significant bits for a bf16 x) into hi + lo, so five products
+//      x Q_hi + x Q_lo + x2_hi R_hi + x2_hi R_lo + x2_lo R_hi
+//    accumulate in FP32 in TMEM and undo the cancellation between
+//    x^2/sigma^2 and 2 x mu/sigma^2;
+// 2. the posteriors (Eq. 2): per row a log-sum-exp over the CTA's 128
+//    components in TMEM, combined over the cluster's CTAs through
+//    distributed shared memory, then gamma written to shared memory as
+//    bfloat16, laid out as the next GEMM's A operand;
+// 3. the statistics GEMM (Algorithm 1 second loop; Phase 2, Algorithm 3):
+//      [S1 | S2hi | S2lo | S0] += gamma^T [X | X2hi | X2lo | 1]
+//    with the tile's own shared-memory X planes as the B operand; the
+//    accumulator stays in TMEM for a whole row share of one frame (a unit)
+//    and is then written to the unit's statistics slot (the paper's
+//    per-block copies of the statistics).
+// The finalise kernel centres the raw moments, scales and normalises.
 //
-// Shared-memory operand layout everywhere: blocks of 16 bf16 columns, each a
-// [rows][16] array of 32-byte rows with the 32-byte swizzle (TMA writes it,
-// the MMA descriptors read it: SBO = 256 B per 8-row group, LBO = block stride).
+// TMEM (512 columns): two log-likelihood buffers of 128 columns (the next
+// tile's GEMM overlaps this tile's softmax) and the statistics accumulator.
+// Shared memory: the GMM operand [Q_hi | Q_lo | R_hi | R_lo] for the CTA's
+// components, resident; a TMA landing buffer for the next tile's x (its
+// load is not held up by the stage still in use); one or two stages of the
+// tile's Y planes; the gamma^T tile; the cluster exchange buffers. Operand layout: blocks of 16
+// bf16 columns, each a [rows][16] array of 32-byte rows with the 32-byte
+// swizzle (TMA writes it; read K-major by the first GEMM and MN-major by the
+// second); gamma^T in 64-component blocks with the 128-byte swizzle.
+//
+// Warp roles (12 warps): 0 TMA producer, 1 MMA issuer, 4-7 and 8-11 two
+// softmax groups taking alternate tiles; warps 2-3 and the tile's softmax
+// group build the tile's Y planes (x copied from the TMA landing buffer,
+// x^2 split, ones).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "fv_bf16.h"
 #include "fv_sm100.cuh"
@@ -45,12 +58,14 @@ using namespace sm100;
 
 namespace {
 
-constexpr int kThreads = 256;          // statistics kernel: 8 warps
-constexpr int kPostThreads = 384;      // posteriors kernel: 12 warps
-constexpr int kTileRows = 128;         // posteriors tile (MMA M)
-constexpr int kStatRows = 64;          // statistics stage rows
-constexpr int kStatStages = 3;
-constexpr uint32_t kGBlk = 64u * kStatRows * 2u;   // one 64-component x 64-row gamma box (8 KB)
+constexpr int kThreads = 384;          // 12 warps
+constexpr int kRows = 128;             // row tile: M of the first GEMM, K of the second
+constexpr int kComps = 128;            // components per CTA: N of the first GEMM, M of the second
+constexpr uint32_t kBlk = kRows * 32u;           // one [128][16] bf16 block with 32-byte rows (4 KB)
+constexpr uint32_t kGHalf = 64u * kRows * 2u;    // 64 components x 128 rows of gamma^T (16 KB)
+constexpr uint32_t kStatCol = 2u * kComps;       // first TMEM column of the statistics accumulator
+constexpr uint32_t kTmemCols = 512;
+constexpr int kMaxSmem = 232448;
 constexpr float kLog2e = 1.4426950408889634f;
 
 // ---- small device helpers ---------------------------------------------------------
@@ -58,60 +73,63 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t *>(&h);
 }
-__device__ __forceinline__ float bf16lo_to_f32(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf16hi_to_f32(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-// x (8 bf16 in a uint4) -> x^2 split into bf16 hi and lo parts (exact: hi + lo == x^2)
+// x (8 bf16 in a uint4) -> x^2 split into bf16 hi and lo parts, exactly:
+// hi = RN(x*x) by a bf16x2 multiply, lo = RN(x*x - hi) by a bf16x2 fused
+// multiply-add (x*x has 16 significant bits, so x*x - hi fits a bf16 and
+// hi + lo == x^2).
 __device__ __forceinline__ void square_split(const uint4 &x, uint4 &hi, uint4 &lo) {
     const uint32_t w[4] = {x.x, x.y, x.z, x.w};
     uint32_t h[4], l[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float a = bf16lo_to_f32(w[i]), b = bf16hi_to_f32(w[i]);
-        const float a2 = a * a, b2 = b * b;
-        const uint32_t hp = pack_bf16x2(a2, b2);
-        h[i] = hp;
-        l[i] = pack_bf16x2(a2 - bf16lo_to_f32(hp), b2 - bf16hi_to_f32(hp));
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&w[i]);
+        const __nv_bfloat162 vh = __hmul2(v, v);
+        const __nv_bfloat162 vl = __hfma2(v, v, __hneg2(vh));
+        h[i] = *reinterpret_cast<const uint32_t *>(&vh);
+        l[i] = *reinterpret_cast<const uint32_t *>(&vl);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// ---- posteriors ------------------------------------------------------------------------
-struct PostArgs {
-    int64_t rows;
-    int ntiles;
-    const int64_t *rows_dev;   // if set, the row count is read here at kernel start (graph replays)
+// ---- fused encoder kernel -------------------------------------------------------------
+struct EncArgs {
     int nkb;        // D16 / 16
     int Kp;
-    int ncta;       // components per CTA (multiple of 16, <= 256)
-    int split;      // CTAs per cluster sharing a row tile (1 or 2)
-    int nstage;     // A-operand stages (1 or 2)
-    uint32_t tmem_cols;
-    const float *cl2;     // [Kp] log-constant times log2(e) (-inf on padding)
-    uint16_t *gamma;      // [rows][Kp] bf16 posteriors
+    int S;          // CTAs per cluster (Kp / 128), each owning 128 components
+    int nstage;     // Y-plane stages (1 or 2)
+    int nslot;      // cluster exchange slots (4, or 2 with a release handshake)
+    int ny;         // 3*D16 + 16 columns of Y
+    int P;          // 3*D16 + 1 floats per component in a slot
+    const float *cl2;         // [Kp] log-constant times log2(e) (-inf on padding)
+    const StatUnit *units;    // row ranges of one frame each
+    const int2 *cl_units;     // per cluster: (first unit, number of units)
+    float *part;              // [slot][P][Kp] statistics slots
     uint32_t *err;
 };
 
-struct PostSmem {
+struct EncSmem {
     // byte offsets from the (1024-aligned) dynamic shared-memory base
-    uint32_t b, a, hx, xchg, bars, misc, total;
-    uint32_t a_stage;   // bytes per A stage
+    uint32_t b, xr, y, y_stage, g, xchg, cl, bars, misc, total;
 };
 
-__host__ __device__ inline PostSmem post_smem(int nkb, int ncta, int nstage, int split) {
-    PostSmem s;
+__host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage, int nslot) {
+    EncSmem s;
     uint32_t off = 0;
-    s.b = off;
-    off += 4u * nkb * ncta * 32u;
-    s.a_stage = 3u * nkb * kTileRows * 32u;
-    s.a = off;
-    off += nstage * s.a_stage;
-    s.hx = off;                       // (max, sum) of each row's two column halves
-    off += 2u * kTileRows * 8u;
-    s.xchg = off;
-    off += split > 1 ? 2u * kTileRows * 8u : 0u;
-    off = (off + 15u) & ~15u;
+    s.b = off;                                   // [Qh | Ql | Rh | Rl] x nkb blocks of 128 components
+    off += 4u * nkb * kBlk;
+    s.xr = off;                                  // TMA landing buffer of the next tile's x
+    off += nkb * kBlk;
+    s.y_stage = (3u * nkb + 1u) * kBlk;          // [X | X2hi | X2lo | 1] blocks of 128 rows
+    s.y = off;
+    off += nstage * s.y_stage;
+    s.g = off;                                   // gamma^T: two 64-component halves
+    off += 2u * kGHalf;
+    s.xchg = off;                                // (max, sum) per row: nslot slots x S ranks
+    off += S > 1 ? (uint32_t)nslot * S * kRows * 8u : 0u;
+    s.cl = off;                                  // the CTA's 128 log-constants
+    off += kComps * 4u;
     s.bars = off;
     off += 24u * 8u;
     s.misc = off;
@@ -120,202 +138,340 @@ __host__ __device__ inline PostSmem post_smem(int nkb, int ncta, int nstage, int
     return s;
 }
 
-// Barrier indices in the barrier array.
-enum { PB_BFULL = 0, PB_XFULL = 1, PB_AFULL = 3, PB_AEMPTY = 5, PB_LFULL = 7, PB_LEMPTY = 9, PB_XCHG = 11,
-       PB_DRAIN = 13, PB_HXFULL = 16, PB_HXFREE = 20 };
+// Barrier indices. A parity wait cannot tell phase n from phase n + 2, so no
+// thread may skip a phase of a barrier it waits on: barriers that complete
+// once per tile but are waited on by one softmax group (which takes every
+// other tile) come in pairs indexed by the tile's parity.
+enum {
+    EB_BFULL = 0,     // GMM operand loaded
+    EB_XRFULL = 1,    // [2] x landing buffer loaded (by tile parity)
+    EB_XRFREE = 3,    // x landing buffer copied out
+    EB_AFULL = 4,     // [2] Y planes of a stage built
+    EB_STFREE = 6,    // [2] both GEMMs done with a tile's stage (by tile parity)
+    EB_LFULL = 8,     // [2] log-likelihoods of a TMEM buffer ready
+    EB_LEMPTY = 10,   // [2] softmax done with a TMEM buffer
+    EB_GFULL = 12,    // gamma^T tile written
+    EB_GFREE = 13,    // statistics GEMM done with gamma^T
+    EB_SDONE = 14,    // [2] a unit's statistics complete in TMEM (by the parity of its last tile)
+    EB_TEMPTY = 16,   // statistics accumulator written out
+    EB_DRAIN = 17,
+    EB_XCHG = 18,     // [4] peers' (max, sum) of a tile arrived, by bytes (per exchange slot)
+    EB_XFREE = 22     // [2] peers' warps have read this CTA's (max, sum) (two-slot form)
+};
 
-__global__ void __launch_bounds__(kPostThreads, 1)
-bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB,
-                       PostArgs p) {
+// Y planes of one tile: x copied from the landing buffer, x^2 split into hi
+// and lo, and the ones block. Rows past the unit's end (the next frame, or
+// zero fill) are zeroed in every plane, so they add nothing to the
+// statistics whatever their posteriors. Thread t of nt.
+__device__ __forceinline__ void build_y(uint8_t *sy, const uint8_t *xr, uint32_t plane, int nkb, int valid, int t,
+                                        int nt) {
+    const int chunks = nkb * kRows * 2;   // 16-byte chunks of the x plane
+    for (int c0 = t; c0 < chunks; c0 += 4 * nt) {
+        uint4 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)   // four loads in flight before any store
+            if (c0 + u * nt < chunks) x[u] = *reinterpret_cast<const uint4 *>(xr + (c0 + u * nt) * 16);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * nt;
+            if (c >= chunks) break;
+            const int row = (c >> 1) & (kRows - 1);   // 32-byte rows; the swizzle stays inside a row
+            uint4 hi, lo;
+            if (row < valid) {
+                square_split(x[u], hi, lo);
+            } else {
+                x[u] = make_uint4(0u, 0u, 0u, 0u);
+                hi = x[u];
+                lo = x[u];
+            }
+            *reinterpret_cast<uint4 *>(sy + c * 16) = x[u];
+            *reinterpret_cast<uint4 *>(sy + plane + c * 16) = hi;
+            *reinterpret_cast<uint4 *>(sy + 2 * plane + c * 16) = lo;
+        }
+    }
+    for (int c = t; c < kRows * 2; c += nt) {
+        const uint32_t one = (c >> 1) < valid ? 0x3F803F80u : 0u;   // bf16 1.0 pairs
+        *reinterpret_cast<uint4 *>(sy + 3 * plane + c * 16) = make_uint4(one, one, one, one);
+    }
+}
+
+// Walks a cluster's units tile by tile (the current unit is held in registers).
+struct TileWalk {
+    const StatUnit *u;
+    int n, ui, t, nt;
+    int64_t row0_;
+    int nrows_, slot_;
+    __device__ TileWalk(const StatUnit *units, int2 cu) : u(units + cu.x), n(cu.y), ui(0), t(0) { load(); }
+    __device__ void load() {
+        if (ui < n) {
+            const StatUnit v = u[ui];
+            row0_ = v.row0;
+            nrows_ = v.nrows;
+            slot_ = v.slot;
+            nt = (nrows_ + kRows - 1) / kRows;
+        } else {
+            nt = 0;
+        }
+    }
+    __device__ bool more() const { return ui < n; }
+    __device__ void next() {
+        if (++t == nt) {
+            t = 0;
+            ++ui;
+            load();
+        }
+    }
+    __device__ int row0() const { return (int)(row0_ + (int64_t)t * kRows); }
+    __device__ int valid() const { return min(kRows, nrows_ - t * kRows); }
+    __device__ bool first() const { return t == 0; }
+    __device__ bool last() const { return t == nt - 1; }
+    __device__ int slot() const { return slot_; }
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, EncArgs p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const PostSmem L = post_smem(p.nkb, p.ncta, p.nstage, p.split);
+    const EncSmem L = enc_smem(p.nkb, p.S, p.nstage, p.nslot);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);   // [0] tmem base, [1] abort
     volatile uint32_t *abort_flag = misc + 1;
 
-    if ((smem_u32(smem) & 1023u) != 0u) {   // layout assumption broken: refuse to run
+    if ((smem_u32(smem) & 1023u) != 0u) {   // layout assumption broken (same in every CTA): refuse to run
         if (threadIdx.x == 0) atomicOr(p.err, kErrAlign);
         return;
     }
-    const uint32_t rank = p.split > 1 ? cluster_ctarank() : 0u;
-    const int cluster_id = blockIdx.x / p.split, nclusters = gridDim.x / p.split;
-    const int64_t nrows = p.rows_dev ? *p.rows_dev : p.rows;
-    const int ntiles = p.rows_dev ? (int)((nrows + kTileRows - 1) / kTileRows) : p.ntiles;
+    const uint32_t rank = p.S > 1 ? cluster_ctarank() : 0u;
+    const int2 cu = p.cl_units[blockIdx.x / p.S];
 
     if (threadIdx.x == 0) {
-        mbar_init(&bars[PB_BFULL], 1);
+        mbar_init(&bars[EB_BFULL], 1);
+        mbar_init(&bars[EB_XRFREE], 6);
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&bars[PB_XFULL + s], 1);
-            mbar_init(&bars[PB_AFULL + s], 2);
-            mbar_init(&bars[PB_AEMPTY + s], 1);
-            mbar_init(&bars[PB_LFULL + s], 1);
-            mbar_init(&bars[PB_LEMPTY + s], 8);
-            mbar_init(&bars[PB_XCHG + s], kTileRows);
+            mbar_init(&bars[EB_XRFULL + s], 1);
+            mbar_init(&bars[EB_AFULL + s], 6);
+            mbar_init(&bars[EB_STFREE + s], 1);
+            mbar_init(&bars[EB_LFULL + s], 1);
+            mbar_init(&bars[EB_LEMPTY + s], 4);
+            mbar_init(&bars[EB_SDONE + s], 1);
         }
-        mbar_init(&bars[PB_DRAIN], 1);
-        for (int q = 0; q < 4; ++q) {
-            mbar_init(&bars[PB_HXFULL + q], 64);
-            mbar_init(&bars[PB_HXFREE + q], 64);
+        mbar_init(&bars[EB_GFULL], 4);
+        mbar_init(&bars[EB_GFREE], 1);
+        mbar_init(&bars[EB_TEMPTY], 4);
+        mbar_init(&bars[EB_DRAIN], 1);
+        if (p.S > 1) {
+            for (int j = 0; j < p.nslot; ++j) mbar_init(&bars[EB_XCHG + j], 1);
+            if (p.nslot == 2)
+                for (int j = 0; j < 2; ++j) mbar_init(&bars[EB_XFREE + j], (uint32_t)(p.S - 1) * 4);
         }
         misc[1] = 0u;
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(&misc[0], p.tmem_cols);
+        tmem_alloc(&misc[0], kTmemCols);
         tmem_relinquish();
     }
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + kComps)
+        reinterpret_cast<float *>(smem + L.cl)[threadIdx.x - 64] = p.cl2[rank * kComps + threadIdx.x - 64];
     tc_fence_before();
     __syncthreads();
-    if (p.split > 1) cluster_sync();   // peers' barriers initialised before any remote arrive
+    if (p.S > 1) cluster_sync();   // peers' barriers initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem = misc[0];
+    const uint32_t plane = (uint32_t)p.nkb * kBlk;   // one of the X, X2hi, X2lo planes
 
-    const uint32_t bw_bytes = (uint32_t)p.ncta * 32u;   // one 16-column block of a B term
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
         prefetch_tmap(&tmX);
         prefetch_tmap(&tmB);
-        mbar_arrive_expect_tx(&bars[PB_BFULL], 4u * p.nkb * bw_bytes);
+        mbar_arrive_expect_tx(&bars[EB_BFULL], 4u * plane);
         for (int t = 0; t < 4; ++t)
             for (int j = 0; j < p.nkb; ++j)
-                tma_load_2d(smem + L.b + (t * p.nkb + j) * bw_bytes, &tmB, &bars[PB_BFULL], j * 16,
-                            t * p.Kp + (int)rank * p.ncta);
-        int last_use[2] = {-1, -1};
+                tma_load_2d(smem + L.b + (t * p.nkb + j) * kBlk, &tmB, &bars[EB_BFULL], j * 16,
+                            t * p.Kp + (int)rank * kComps);
+        // x of tile i lands in the landing buffer as soon as tile i - 1 has
+        // been copied out of it, well before tile i's stage is free
+        int last = -1;
         int i = 0;
-        for (int tile = cluster_id; tile < ntiles; tile += nclusters, ++i) {
-            const int s = i % p.nstage, u = i / p.nstage;
-            if (u > 0 && !mbar_wait(&bars[PB_AEMPTY + s], (u - 1) & 1, abort_flag, p.err)) break;
-            uint8_t *ax = smem + L.a + s * L.a_stage;
-            mbar_arrive_expect_tx(&bars[PB_XFULL + s], (uint32_t)p.nkb * kTileRows * 32u);
+        for (TileWalk w(p.units, cu); w.more(); w.next(), ++i) {
+            if (i > 0 && !mbar_wait(&bars[EB_XRFREE], (i - 1) & 1, abort_flag, p.err)) break;
+            mbar_arrive_expect_tx(&bars[EB_XRFULL + (i & 1)], plane);
             for (int j = 0; j < p.nkb; ++j)
-                tma_load_2d(ax + j * kTileRows * 32, &tmX, &bars[PB_XFULL + s], j * 16, tile * kTileRows);
-            last_use[s] = u;
+                tma_load_2d(smem + L.xr + j * kBlk, &tmX, &bars[EB_XRFULL + (i & 1)], j * 16, w.row0());
+            last = i;
         }
         // wait (bounded, even when aborting) for this thread's copies still in flight
-        for (int s = 0; s < 2; ++s) {
-            if (last_use[s] < 0) continue;
-            mbar_drain(&bars[PB_XFULL + s], last_use[s] & 1, 200000000ll);
-        }
-        mbar_drain(&bars[PB_BFULL], 0, 200000000ll);
+        if (last >= 0) mbar_drain(&bars[EB_XRFULL + (last & 1)], (last >> 1) & 1, 200000000ll);
+        mbar_drain(&bars[EB_BFULL], 0, 200000000ll);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc = idesc_bf16(kTileRows, p.ncta, false, false);
-        const uint32_t sB = smem_u32(smem + L.b);
-        bool ok = mbar_wait(&bars[PB_BFULL], 0, abort_flag, p.err);
-        int i = 0;
-        bool issued = false;
-        for (int tile = cluster_id; ok && tile < ntiles; tile += nclusters, ++i) {
-            const int s = i % p.nstage, b = i & 1;
-            if (!mbar_wait(&bars[PB_AFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
-            if (i >= 2 && !mbar_wait(&bars[PB_LEMPTY + b], ((i >> 1) - 1) & 1, abort_flag, p.err)) break;
-            tc_fence_after();
-            const uint32_t sA = smem_u32(smem + L.a + s * L.a_stage);
-            const uint32_t d = tmem + (uint32_t)(b * p.ncta);
-            const uint32_t ablk = kTileRows * 32u;   // one 16-column block of an A operand
-            uint32_t acc = 0;
-            for (int j = 0; j < p.nkb; ++j) {
-                const uint32_t ax = sA + (0 * p.nkb + j) * ablk;
-                const uint32_t ah = sA + (1 * p.nkb + j) * ablk;
-                const uint32_t al = sA + (2 * p.nkb + j) * ablk;
-                const uint32_t bqh = sB + (0 * p.nkb + j) * bw_bytes;
-                const uint32_t bql = sB + (1 * p.nkb + j) * bw_bytes;
-                const uint32_t brh = sB + (2 * p.nkb + j) * bw_bytes;
-                const uint32_t brl = sB + (3 * p.nkb + j) * bw_bytes;
-                mma_bf16(d, sdesc_sw32(ax, 16, 256), sdesc_sw32(bqh, 16, 256), idesc, acc);
-                acc = 1;
-                mma_bf16(d, sdesc_sw32(ax, 16, 256), sdesc_sw32(bql, 16, 256), idesc, 1);
-                mma_bf16(d, sdesc_sw32(ah, 16, 256), sdesc_sw32(brh, 16, 256), idesc, 1);
-                mma_bf16(d, sdesc_sw32(ah, 16, 256), sdesc_sw32(brl, 16, 256), idesc, 1);
-                mma_bf16(d, sdesc_sw32(al, 16, 256), sdesc_sw32(brh, 16, 256), idesc, 1);
+        // Order: L(i), then the statistics GEMM of tile i - lag, where lag is
+        // one with two stages (the next tile's log-likelihoods run while this
+        // tile's softmax works) and zero with one stage.
+        const uint32_t idesc_l = idesc_bf16(kRows, kComps, false, false);
+        const uint32_t idesc_s = idesc_bf16(kComps, p.ny, true, true);
+        const uint32_t sB = smem_u32(smem + L.b), sG = smem_u32(smem + L.g);
+        const int lag = p.nstage - 1;
+        struct Pend {
+            int i, s, ui;
+            bool first, last;
+        } prev = {-1, 0, 0, false, false};
+        auto stats = [&](const Pend &t) -> bool {
+            if (t.first && t.ui > 0) {   // the previous unit's accumulator has been written out
+                if (!mbar_wait(&bars[EB_TEMPTY], (t.ui - 1) & 1, abort_flag, p.err)) return false;
             }
-            mma_commit(&bars[PB_AEMPTY + s]);
-            mma_commit(&bars[PB_LFULL + b]);
+            if (!mbar_wait(&bars[EB_GFULL], t.i & 1, abort_flag, p.err)) return false;
+            tc_fence_after();
+            const uint32_t sy = smem_u32(smem + L.y + t.s * L.y_stage);
+            for (int q = 0; q < kRows / 16; ++q) {
+                // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
+                // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
+                // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
+                const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
+                const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                mma_bf16(tmem + kStatCol, a, b, idesc_s, (t.first && q == 0) ? 0u : 1u);
+            }
+            mma_commit(&bars[EB_GFREE]);
+            mma_commit(&bars[EB_STFREE + (t.i & 1)]);
+            if (t.last) mma_commit(&bars[EB_SDONE + (t.i & 1)]);
+            return true;
+        };
+        bool ok = mbar_wait(&bars[EB_BFULL], 0, abort_flag, p.err);
+        bool issued = false;
+        int i = 0;
+        for (TileWalk w(p.units, cu); ok && w.more(); w.next(), ++i) {
+            const int s = i % p.nstage, b = i & 1;
+            if (!mbar_wait(&bars[EB_AFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
+            if (i >= 2 && !mbar_wait(&bars[EB_LEMPTY + b], ((i >> 1) - 1) & 1, abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + L.y + s * L.y_stage);
+            const uint32_t d = tmem + (uint32_t)(b * kComps);
+            for (int j = 0; j < p.nkb; ++j) {
+                const uint64_t ax = sdesc_sw32(sA + j * kBlk, 16, 256);
+                const uint64_t ah = sdesc_sw32(sA + plane + j * kBlk, 16, 256);
+                const uint64_t al = sdesc_sw32(sA + 2 * plane + j * kBlk, 16, 256);
+                const uint64_t bqh = sdesc_sw32(sB + (0 * p.nkb + j) * kBlk, 16, 256);
+                const uint64_t bql = sdesc_sw32(sB + (1 * p.nkb + j) * kBlk, 16, 256);
+                const uint64_t brh = sdesc_sw32(sB + (2 * p.nkb + j) * kBlk, 16, 256);
+                const uint64_t brl = sdesc_sw32(sB + (3 * p.nkb + j) * kBlk, 16, 256);
+                mma_bf16(d, ax, bqh, idesc_l, j > 0 ? 1u : 0u);
+                mma_bf16(d, ax, bql, idesc_l, 1u);
+                mma_bf16(d, ah, brh, idesc_l, 1u);
+                mma_bf16(d, ah, brl, idesc_l, 1u);
+                mma_bf16(d, al, brh, idesc_l, 1u);
+            }
+            mma_commit(&bars[EB_LFULL + b]);
             issued = true;
+            const Pend cur = {i, s, w.ui, w.first(), w.last()};
+            if (lag == 0) {
+                ok = stats(cur);
+            } else {
+                if (prev.i >= 0) ok = stats(prev);
+                prev = cur;
+            }
         }
+        if (ok && lag > 0 && prev.i >= 0) stats(prev);
         if (issued) {   // every issued MMA has finished before TMEM is released
-            mma_commit(&bars[PB_DRAIN]);
-            mbar_drain(&bars[PB_DRAIN], 0, 2000000000ll);
+            mma_commit(&bars[EB_DRAIN]);
+            mbar_drain(&bars[EB_DRAIN], 0, 2000000000ll);
         }
     } else if (warp == 2 || warp == 3) {
-        // ---------------- x^2 hi/lo builders ----------------
-        const int t = threadIdx.x - 64;
-        const int chunks = p.nkb * kTileRows * 2;   // 16-byte chunks of the x blocks
+        // ---------------- Y builders (with the softmax group of the tile) ----------------
         int i = 0;
-        for (int tile = cluster_id; tile < ntiles; tile += nclusters, ++i) {
-            const int s = i % p.nstage;
-            if (!mbar_wait(&bars[PB_XFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
-            uint8_t *sa = smem + L.a + s * L.a_stage;
-            const uint32_t plane = (uint32_t)p.nkb * kTileRows * 32u;
-            for (int c = t; c < chunks; c += 64) {
-                const uint4 x = *reinterpret_cast<const uint4 *>(sa + c * 16);
-                uint4 hi, lo;
-                square_split(x, hi, lo);
-                *reinterpret_cast<uint4 *>(sa + plane + c * 16) = hi;
-                *reinterpret_cast<uint4 *>(sa + 2 * plane + c * 16) = lo;
-            }
+        for (TileWalk w(p.units, cu); w.more(); w.next(), ++i) {
+            const int s = i % p.nstage, j = i - p.nstage;   // tile j used this stage before
+            if (!mbar_wait(&bars[EB_XRFULL + (i & 1)], (i >> 1) & 1, abort_flag, p.err)) break;
+            if (j >= 0 && !mbar_wait(&bars[EB_STFREE + (j & 1)], (j >> 1) & 1, abort_flag, p.err)) break;
+            build_y(smem + L.y + s * L.y_stage, smem + L.xr, plane, p.nkb, w.valid(), threadIdx.x - 64, 192);
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bars[PB_AFULL + s]);
+            if (lane == 0) {
+                mbar_arrive(&bars[EB_XRFREE]);
+                mbar_arrive(&bars[EB_AFULL + s]);
+            }
         }
     } else if (warp >= 4) {
-        // ---------------- softmax epilogue ----------------
-        // Two warps per TMEM lane quadrant: warp 4+q and 8+q own rows
-        // 32q..32q+31, each over half of the CTA's columns. Pass A reads L,
-        // forms y = l log2(e) + c log2(e), keeps an online row max/sum with a
-        // reference max per 32-column chunk and stores 2^(y - ref) back into
-        // TMEM; the halves (and, with a component split, the peer CTA) combine
-        // their (max, sum); pass B rescales each chunk and writes bf16.
-        const int q = warp & 3, h = (warp - 4) >> 2;
+        // ---------------- softmax groups ----------------
+        // Group grp (warps 4-7 or 8-11) takes the tiles with i % 2 == grp and
+        // TMEM buffer grp; warp 4*(grp+1)+q owns rows 32q..32q+31 (its TMEM lane
+        // quadrant), one row per thread, over the CTA's 128 components in four
+        // 32-column chunks. Pass A forms y = l log2(e) + c log2(e), keeps an
+        // online row max/sum with a reference max per chunk and stores
+        // 2^(y - ref) back into TMEM; the cluster's CTAs combine their (max,
+        // sum); pass B rescales each chunk and writes bf16 gamma^T to shared
+        // memory. The group that finishes a unit's last tile then writes the
+        // unit's statistics from TMEM to its slot.
+        const int grp = (warp - 4) >> 2, q = warp & 3;
         const int r = q * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        const int nh = p.ncta / 64;          // 32-column chunks per half (2, 3 or 4)
-        const int c0 = h * nh;
-        float2 *hx = reinterpret_cast<float2 *>(smem + L.hx);
+        const float *cl = reinterpret_cast<const float *>(smem + L.cl);
         float2 *xbuf = reinterpret_cast<float2 *>(smem + L.xchg);
-        const float *cl = p.cl2 + rank * p.ncta;
-        int i = 0;
-        for (int tile = cluster_id; tile < ntiles; tile += nclusters, ++i) {
-            const int b = i & 1;
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars[PB_LFULL + b], (i >> 1) & 1, abort_flag, p.err))) break;
+        uint8_t *gsm = smem + L.g + r * 128;   // this row in the first 64-component half
+        const int sw = r & 7;                  // 128-byte swizzle: 16-byte chunk j sits at j ^ (row & 7)
+        int i = 0, nflush = 0;
+        bool ok = true;
+        for (TileWalk w(p.units, cu); ok && w.more(); w.next(), ++i) {
+            if ((i & 1) != grp) continue;
+            {   // help build this tile's Y planes (the group is idle until its log-likelihoods exist)
+                const int s = i % p.nstage, j = i - p.nstage;   // tile j used this stage before
+                if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_XRFULL + (i & 1)], (i >> 1) & 1, abort_flag, p.err)))
+                    break;
+                if (j >= 0 && !__all_sync(0xffffffffu, mbar_wait(&bars[EB_STFREE + (j & 1)], (j >> 1) & 1,
+                                                                 abort_flag, p.err)))
+                    break;
+                build_y(smem + L.y + s * L.y_stage, smem + L.xr, plane, p.nkb, w.valid(), 64 + q * 32 + lane, 192);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&bars[EB_XRFREE]);
+                    mbar_arrive(&bars[EB_AFULL + s]);
+                }
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_LFULL + grp], (i >> 1) & 1, abort_flag, p.err))) break;
             tc_fence_after();
-            const uint32_t ta = lane_base + (uint32_t)(b * p.ncta);
+            const uint32_t ta = lane_base + (uint32_t)(grp * kComps);
             float m = -INFINITY, z = 0.f;
-            float mc[4] = {0.f, 0.f, 0.f, 0.f};
+            float mc[4];
             uint32_t ra[32], rb[32];
-            // software pipeline: the next chunk's TMEM load is in flight while
-            // this chunk is processed; this chunk's constants are requested
-            // before waiting on its TMEM load
-            tmem_ld32_issue(ta + c0 * 32, ra);
+            // the next chunk's TMEM load is in flight while this chunk is
+            // processed; this chunk's constants are requested before waiting
+            tmem_ld32_issue(ta, ra);
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                if (cc >= nh) break;
-                const int c = c0 + cc;
-                uint32_t(&cur)[32] = (cc & 1) ? rb : ra;
-                uint32_t(&nxt)[32] = (cc & 1) ? ra : rb;
+            for (int c = 0; c < 4; ++c) {
+                uint32_t(&cur)[32] = (c & 1) ? rb : ra;
+                uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
                 float4 ccur[8];
 #pragma unroll
-                for (int k4 = 0; k4 < 8; ++k4) ccur[k4] = __ldg(reinterpret_cast<const float4 *>(cl + c * 32) + k4);
+                for (int k4 = 0; k4 < 8; ++k4) ccur[k4] = reinterpret_cast<const float4 *>(cl + c * 32)[k4];
                 tmem_ld_wait(cur);
-                if (cc + 1 < nh) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
-                float y[32];
-                float cm0 = -INFINITY, cm1 = -INFINITY;
+                if (c < 3) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
+                // y overwrites l in place (register pressure); four independent
+                // max chains
+                float cm0 = -INFINITY, cm1 = -INFINITY, cm2 = -INFINITY, cm3 = -INFINITY;
 #pragma unroll
                 for (int k4 = 0; k4 < 8; ++k4) {
-                    y[4 * k4 + 0] = fmaf(__uint_as_float(cur[4 * k4 + 0]), kLog2e, ccur[k4].x);
-                    y[4 * k4 + 1] = fmaf(__uint_as_float(cur[4 * k4 + 1]), kLog2e, ccur[k4].y);
-                    y[4 * k4 + 2] = fmaf(__uint_as_float(cur[4 * k4 + 2]), kLog2e, ccur[k4].z);
-                    y[4 * k4 + 3] = fmaf(__uint_as_float(cur[4 * k4 + 3]), kLog2e, ccur[k4].w);
-                    cm0 = fmaxf(cm0, fmaxf(y[4 * k4 + 0], y[4 * k4 + 1]));
-                    cm1 = fmaxf(cm1, fmaxf(y[4 * k4 + 2], y[4 * k4 + 3]));
+                    const float y0 = fmaf(__uint_as_float(cur[4 * k4 + 0]), kLog2e, ccur[k4].x);
+                    const float y1 = fmaf(__uint_as_float(cur[4 * k4 + 1]), kLog2e, ccur[k4].y);
+                    const float y2 = fmaf(__uint_as_float(cur[4 * k4 + 2]), kLog2e, ccur[k4].z);
+                    const float y3 = fmaf(__uint_as_float(cur[4 * k4 + 3]), kLog2e, ccur[k4].w);
+                    cm0 = fmaxf(cm0, y0);
+                    cm1 = fmaxf(cm1, y1);
+                    cm2 = fmaxf(cm2, y2);
+                    cm3 = fmaxf(cm3, y3);
+                    cur[4 * k4 + 0] = __float_as_uint(y0);
+                    cur[4 * k4 + 1] = __float_as_uint(y1);
+                    cur[4 * k4 + 2] = __float_as_uint(y2);
+                    cur[4 * k4 + 3] = __float_as_uint(y3);
                 }
-                const float mn = fmaxf(m, fmaxf(cm0, cm1));
+                const float mn = fmaxf(m, fmaxf(fmaxf(cm0, cm1), fmaxf(cm2, cm3)));
                 const float mref = (mn == -INFINITY) ? 0.f : mn;
                 float z0 = z * ex2_approx(m - mref), z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
                 for (int k = 0; k < 32; k += 4) {
-                    const float e0 = ex2_approx(y[k + 0] - mref), e1 = ex2_approx(y[k + 1] - mref);
-                    const float e2 = ex2_approx(y[k + 2] - mref), e3 = ex2_approx(y[k + 3] - mref);
+                    const float e0 = ex2_approx(__uint_as_float(cur[k + 0]) - mref);
+                    const float e1 = ex2_approx(__uint_as_float(cur[k + 1]) - mref);
+                    const float e2 = ex2_approx(__uint_as_float(cur[k + 2]) - mref);
+                    const float e3 = ex2_approx(__uint_as_float(cur[k + 3]) - mref);
                     z0 += e0;
                     z1 += e1;
                     z2 += e2;
@@ -326,297 +482,122 @@ bf16_posteriors_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_con
                     cur[k + 3] = __float_as_uint(e3);
                 }
                 z = (z0 + z1) + (z2 + z3);
-                tmem_st32_u(ta + c * 32, cur);
-                mc[cc] = mref;
+                tmem_st32_nowait(ta + c * 32, cur);
+                mc[c] = mref;
                 m = mn;
             }
-            // combine the two column halves of the row (bounded handshakes:
-            // the partner warp has read the previous tile's value before this
-            // one is written, and has written this tile's before it is read)
-            if (i > 0 && !__all_sync(0xffffffffu, mbar_wait(&bars[PB_HXFREE + q], (i - 1) & 1, abort_flag, p.err)))
-                break;
-            hx[h * kTileRows + r] = make_float2(m, z);
-            mbar_arrive(&bars[PB_HXFULL + q]);
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars[PB_HXFULL + q], i & 1, abort_flag, p.err))) break;
-            const float2 o = hx[(h ^ 1) * kTileRows + r];
-            mbar_arrive(&bars[PB_HXFREE + q]);
-            float M = fmaxf(m, o.x);
-            float Mref = (M == -INFINITY) ? 0.f : M;
-            float Z = z * ex2_approx(m - Mref) + o.y * ex2_approx(o.x - Mref);
-            if (p.split > 1) {
-                const uint32_t peer = rank ^ 1u;
-                if (h == 0) {
-                    st_cluster_f32x2(mapa(smem_u32(&xbuf[b * kTileRows + r]), peer), M, Z);
-                    mbar_arrive_remote(mapa(smem_u32(&bars[PB_XCHG + b]), peer));
-                }
-                if (!__all_sync(0xffffffffu, mbar_wait(&bars[PB_XCHG + b], (i >> 1) & 1, abort_flag, p.err, true)))
+            tmem_st_wait();   // the exponentials are in TMEM before pass B reads them back
+            // (max, sum) over the cluster, combined in rank order so that every
+            // CTA normalises with the same value. Exchange slot j = i % nslot
+            // of every CTA receives the peers' values for tile i by st.async
+            // (counted in bytes on XCHG[j], which this CTA arms once per use).
+            // With four slots a peer writes slot j again only for tile i + 4,
+            // after this group's contribution to tile i + 2, which follows this
+            // read; with two slots every warp releases the slot (XFREE).
+            float M = -INFINITY, Z = 0.f;
+            if (p.S > 1) {
+                const int j = i % p.nslot;
+                float2 *xb = xbuf + j * p.S * kRows;
+                if (q == 0 && lane == 0)
+                    mbar_arrive_expect_tx(&bars[EB_XCHG + j], (uint32_t)(p.S - 1) * kRows * 8u);
+                if (p.nslot == 2 && i >= 2 &&
+                    !__all_sync(0xffffffffu,
+                                mbar_wait(&bars[EB_XFREE + grp], ((i >> 1) - 1) & 1, abort_flag, p.err, true)))
                     break;
-                const float2 po = xbuf[b * kTileRows + r];
-                const float M2 = fmaxf(M, po.x);
-                const float M2ref = (M2 == -INFINITY) ? 0.f : M2;
-                Z = Z * ex2_approx(M - M2ref) + po.y * ex2_approx(po.x - M2ref);
-                M = M2;
-                Mref = M2ref;
+                for (int pr = 0; pr < p.S; ++pr) {
+                    if (pr == (int)rank) continue;
+                    st_async_f32x2(mapa(smem_u32(&xb[rank * kRows + r]), (uint32_t)pr), m, z,
+                                   mapa(smem_u32(&bars[EB_XCHG + j]), (uint32_t)pr));
+                }
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(&bars[EB_XCHG + j], (i / p.nslot) & 1, abort_flag, p.err, true)))
+                    break;
+                for (int pr = 0; pr < p.S; ++pr) {
+                    const float2 v = pr == (int)rank ? make_float2(m, z) : xb[pr * kRows + r];
+                    const float Mn = fmaxf(M, v.x);
+                    const float ref = (Mn == -INFINITY) ? 0.f : Mn;
+                    Z = Z * ex2_approx(M - ref) + v.y * ex2_approx(v.x - ref);
+                    M = Mn;
+                }
+                if (p.nslot == 2) {
+                    __syncwarp();   // the warp's reads are done before its release
+                    if (lane == 0)
+                        for (int pr = 0; pr < p.S; ++pr)
+                            if (pr != (int)rank)
+                                mbar_arrive_remote(mapa(smem_u32(&bars[EB_XFREE + grp]), (uint32_t)pr));
+                }
+            } else {
+                M = m;
+                Z = z;
             }
+            const float Mref = (M == -INFINITY) ? 0.f : M;
             const float inv = 1.0f / Z;
-            // pass B: normalised posteriors -> bf16 global (next chunk's load in flight)
-            const int64_t row = (int64_t)tile * kTileRows + r;
-            uint16_t *g = p.gamma + row * p.Kp + rank * p.ncta;
-            tmem_ld32_issue(ta + c0 * 32, ra);
+            // the statistics GEMM of the previous tile has read gamma^T. No
+            // phase can be skipped here: L(i) was issued after the statistics
+            // GEMM of tile i - 2, so that phase completed before LFULL(i).
+            if (i >= 1 && !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], (i - 1) & 1, abort_flag, p.err))) break;
+            // pass B: normalised posteriors -> bf16 gamma^T (next chunk's load in flight)
+            tmem_ld32_issue(ta, ra);
             tmem_ld_wait(ra);
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                if (cc >= nh) break;
-                const int c = c0 + cc;
-                uint32_t(&cur)[32] = (cc & 1) ? rb : ra;
-                uint32_t(&nxt)[32] = (cc & 1) ? ra : rb;
-                if (cc + 1 < nh) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
-                const float sc = ex2_approx(mc[cc] - Mref) * inv;
-                if (row < nrows) {   // 64 bytes of the row: two full 32-byte sectors
-                    uint32_t pk[16];
+            for (int c = 0; c < 4; ++c) {
+                uint32_t(&cur)[32] = (c & 1) ? rb : ra;
+                uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
+                if (c < 3) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
+                const float sc = ex2_approx(mc[c] - Mref) * inv;
+                uint8_t *gh = gsm + (c >> 1) * kGHalf;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        pk[k] = pack_bf16x2(__uint_as_float(cur[2 * k]) * sc, __uint_as_float(cur[2 * k + 1]) * sc);
-                    st_global_v8(g + c * 32, pk);
-                    st_global_v8(g + c * 32 + 16, pk + 8);
+                for (int k = 0; k < 4; ++k) {   // 16-byte chunk (c & 1) * 4 + k of the 128-byte row
+                    uint4 v;
+                    v.x = pack_bf16x2(__uint_as_float(cur[8 * k + 0]) * sc, __uint_as_float(cur[8 * k + 1]) * sc);
+                    v.y = pack_bf16x2(__uint_as_float(cur[8 * k + 2]) * sc, __uint_as_float(cur[8 * k + 3]) * sc);
+                    v.z = pack_bf16x2(__uint_as_float(cur[8 * k + 4]) * sc, __uint_as_float(cur[8 * k + 5]) * sc);
+                    v.w = pack_bf16x2(__uint_as_float(cur[8 * k + 6]) * sc, __uint_as_float(cur[8 * k + 7]) * sc);
+                    *reinterpret_cast<uint4 *>(gh + ((((c & 1) * 4 + k) ^ sw) << 4)) = v;
                 }
-                if (cc + 1 < nh) tmem_ld_wait(nxt);
+                if (c < 3) tmem_ld_wait(nxt);
             }
+            fence_proxy_async_smem();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bars[PB_LEMPTY + b]);
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (p.split > 1) cluster_sync();   // no remote access into a CTA that has exited
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem, p.tmem_cols);
-    }
-}
-
-// ---- statistics -----------------------------------------------------------------------
-struct StatArgs {
-    int nkb;       // D16 / 16
-    int D;
-    int Kp;
-    int sc;        // components per CTA (128 or 256)
-    int ny;        // 3*D16 + 16 columns of Y
-    int P;         // 3*D16 + 1 floats per component in a slot
-    uint32_t tmem_cols;
-    const StatUnit *units;
-    const int2 *cta_units;   // per CTA: (first unit, number of units)
-    float *part;
-    uint32_t *err;
-};
-
-struct StatSmem {
-    uint32_t g_stage, y_stage, stage, bars, misc, total;
-};
-__host__ __device__ inline StatSmem stat_smem(int nkb, int sc) {
-    StatSmem s;
-    s.g_stage = (uint32_t)(sc / 16) * kStatRows * 32u;
-    s.y_stage = (uint32_t)(3 * nkb + 1) * kStatRows * 32u;
-    s.stage = s.g_stage + s.y_stage;
-    s.bars = kStatStages * s.stage;
-    s.misc = s.bars + 16u * 8u;
-    s.total = s.misc + 16u;
-    return s;
-}
-enum { SB_FULL = 0, SB_READY = 3, SB_EMPTY = 6, SB_DONE = 9, SB_TEMPTY = 10, SB_DRAIN = 11 };
-
-// Persistent: CTA (blockIdx.x, blockIdx.y) walks its units (row segments of
-// one frame, contiguous in the packed rows) through one continuous ring of
-// 64-row stages for the component group blockIdx.y; after each unit the
-// accumulator is flushed from TMEM to the unit's slot.
-__global__ void __launch_bounds__(kThreads, 1)
-bf16_stats_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmX, StatArgs p) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const StatSmem L = stat_smem(p.nkb, p.sc);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
-    uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);
-    volatile uint32_t *abort_flag = misc + 1;
-    if ((smem_u32(smem) & 1023u) != 0u) {
-        if (threadIdx.x == 0) atomicOr(p.err, kErrAlign);
-        return;
-    }
-    const int2 cu = p.cta_units[blockIdx.x];
-    const int kc0 = blockIdx.y * p.sc;
-    const int nchunk = p.sc / 128;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStatStages; ++s) {
-            mbar_init(&bars[SB_FULL + s], 1);
-            mbar_init(&bars[SB_READY + s], 6);
-            mbar_init(&bars[SB_EMPTY + s], 1);
-        }
-        mbar_init(&bars[SB_DONE], 1);
-        mbar_init(&bars[SB_TEMPTY], 4);
-        mbar_init(&bars[SB_DRAIN], 1);
-        misc[1] = 0u;
-        fence_mbar_init();
-    }
-    if (warp == 1) {
-        tmem_alloc(&misc[0], p.tmem_cols);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = misc[0];
-    const uint32_t blk = kStatRows * 32u;   // bytes of one 16-column block
-
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
-        prefetch_tmap(&tmG);
-        prefetch_tmap(&tmX);
-        int last_use[kStatStages] = {-1, -1, -1};
-        int gs = 0;
-        bool ok = true;
-        for (int ui = 0; ok && ui < cu.y; ++ui) {
-            const StatUnit u = p.units[cu.x + ui];
-            const int nit = (u.nrows + kStatRows - 1) / kStatRows;
-            for (int it = 0; it < nit; ++it, ++gs) {
-                const int s = gs % kStatStages, use = gs / kStatStages;
-                if (use > 0 && !mbar_wait(&bars[SB_EMPTY + s], (use - 1) & 1, abort_flag, p.err)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t *sg = smem + s * L.stage;
-                uint8_t *sy = sg + L.g_stage;
-                const int y = (int)(u.row0 + (int64_t)it * kStatRows);
-                mbar_arrive_expect_tx(&bars[SB_FULL + s], (uint32_t)(p.sc / 16 + p.nkb) * blk);
-                for (int cb = 0; cb < p.sc / 64; ++cb)   // 64 components x 64 rows, 128-byte rows
-                    tma_load_2d(sg + cb * kGBlk, &tmG, &bars[SB_FULL + s], kc0 + cb * 64, y);
-                for (int j = 0; j < p.nkb; ++j) tma_load_2d(sy + j * blk, &tmX, &bars[SB_FULL + s], j * 16, y);
-                last_use[s] = use;
+            if (lane == 0) {
+                mbar_arrive(&bars[EB_GFULL]);
+                mbar_arrive(&bars[EB_LEMPTY + grp]);
             }
-        }
-        for (int s = 0; s < kStatStages; ++s) {
-            if (last_use[s] < 0) continue;
-            mbar_drain(&bars[SB_FULL + s], last_use[s] & 1, 200000000ll);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        const uint32_t idesc = idesc_bf16(128, p.ny, true, true);
-        bool issued = false, ok = true;
-        int gs = 0;
-        for (int ui = 0; ok && ui < cu.y; ++ui) {
-            const StatUnit u = p.units[cu.x + ui];
-            const int nit = (u.nrows + kStatRows - 1) / kStatRows;
-            if (ui > 0) {   // the epilogue has read the previous unit's accumulator
-                if (!mbar_wait(&bars[SB_TEMPTY], (ui - 1) & 1, abort_flag, p.err)) break;
-                tc_fence_after();
-            }
-            for (int it = 0; it < nit; ++it, ++gs) {
-                const int s = gs % kStatStages;
-                if (!mbar_wait(&bars[SB_READY + s], (gs / kStatStages) & 1, abort_flag, p.err)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t sg = smem_u32(smem + s * L.stage);
-                const uint32_t sy = sg + L.g_stage;
-                for (int q = 0; q < kStatRows / 16; ++q) {
-                    for (int c = 0; c < nchunk; ++c) {
-                        // gamma^T, MN-major, 128-byte swizzle: 64-component blocks kGBlk
-                        // apart, 8-row groups 1024 B apart, 16 rows per K step
-                        const uint64_t a = sdesc_sw128(sg + c * 2 * kGBlk + q * 2048, kGBlk, 1024);
-                        const uint64_t b = sdesc_sw32(sy + q * 512, blk, 256);
-                        mma_bf16(tmem + (uint32_t)(c * p.ny), a, b, idesc, (it > 0 || q > 0) ? 1u : 0u);
-                    }
-                }
-                mma_commit(&bars[SB_EMPTY + s]);
-                issued = true;
-            }
-            if (ok) mma_commit(&bars[SB_DONE]);
-        }
-        if (issued) {   // every issued MMA has finished before TMEM is released
-            mma_commit(&bars[SB_DRAIN]);
-            mbar_drain(&bars[SB_DRAIN], 0, 2000000000ll);
-        }
-    } else if (warp >= 2) {
-        // ---------------- Y builders (warps 2-7); warps 4-7 also flush TMEM ----------------
-        const int t = threadIdx.x - 64;          // 0..191
-        const int xchunks = p.nkb * kStatRows * 2;
-        const uint32_t plane = (uint32_t)p.nkb * blk;
-        int gs = 0;
-        bool ok = true;
-        for (int ui = 0; ok && ui < cu.y; ++ui) {
-            const StatUnit u = p.units[cu.x + ui];
-            const int nit = (u.nrows + kStatRows - 1) / kStatRows;
-            for (int it = 0; it < nit; ++it, ++gs) {
-                const int s = gs % kStatStages;
-                if (!mbar_wait(&bars[SB_FULL + s], (gs / kStatStages) & 1, abort_flag, p.err)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t *sy = smem + s * L.stage + L.g_stage;
-                const int valid = min(kStatRows, u.nrows - it * kStatRows);
-                for (int c = t; c < xchunks; c += 192) {
-                    const int row = (c >> 1) % kStatRows;   // 32-byte rows; the swizzle stays inside a row
-                    uint4 x = *reinterpret_cast<const uint4 *>(sy + c * 16);
-                    uint4 hi, lo;
-                    if (row < valid) {
-                        square_split(x, hi, lo);
-                    } else {
-                        x = make_uint4(0, 0, 0, 0);
-                        hi = x;
-                        lo = x;
-                        *reinterpret_cast<uint4 *>(sy + c * 16) = x;
-                    }
-                    *reinterpret_cast<uint4 *>(sy + plane + c * 16) = hi;
-                    *reinterpret_cast<uint4 *>(sy + 2 * plane + c * 16) = lo;
-                }
-                for (int c = t; c < kStatRows * 2; c += 192) {
-                    const int row = c >> 1;
-                    const uint32_t one = row < valid ? 0x3F803F80u : 0u;   // bf16 1.0 pairs
-                    *reinterpret_cast<uint4 *>(sy + 3 * plane + c * 16) = make_uint4(one, one, one, one);
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bars[SB_READY + s]);
-            }
-            if (!ok || warp < 4) continue;
-            // flush this unit's accumulator: TMEM -> slot part[slot][j][Kp]
-            const int q = warp & 3;
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars[SB_DONE], ui & 1, abort_flag, p.err))) {
-                ok = false;
-                break;
-            }
+            if (!w.last()) continue;
+            // the unit's statistics: TMEM -> slot part[slot][j][Kp]. Slot
+            // columns follow the TMEM columns ([S1 | S2hi | S2lo] blocks of
+            // D16, then S0, the first ones column), so this is a copy; two
+            // 32-column loads are in flight at a time.
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_SDONE + grp], nflush & 1, abort_flag, p.err))) break;
+            ++nflush;
             tc_fence_after();
-            // slot columns follow the TMEM columns: [S1 | S2hi | S2lo] blocks of
-            // D16, then S0 (the first ones column), so the flush is a copy; two
-            // 32-column TMEM loads are in flight at a time
-            for (int c = 0; c < nchunk; ++c) {
-                const int k = kc0 + c * 128 + q * 32 + lane;
-                float *dst = p.part + (size_t)u.slot * p.Kp * p.P + k;
-                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * p.ny);
-                for (int n0 = 0; n0 < p.P; n0 += 64) {
-                    uint32_t va[32], vb[32];
-                    tmem_ld32_issue(ta + n0, va);
-                    tmem_ld32_issue(ta + n0 + 32, vb);
-                    tmem_ld_wait(va);
-                    tmem_ld_wait(vb);
+            const int k = (int)rank * kComps + r;
+            float *dst = p.part + (size_t)w.slot() * p.Kp * p.P + k;
+            const uint32_t ts = lane_base + kStatCol;
+            for (int n0 = 0; n0 < p.P; n0 += 64) {
+                uint32_t va[32], vb[32];
+                tmem_ld32_issue(ts + n0, va);
+                tmem_ld32_issue(ts + n0 + 32, vb);
+                tmem_ld_wait(va);
+                tmem_ld_wait(vb);
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        if (n0 + e < p.P) dst[(size_t)(n0 + e) * p.Kp] = __uint_as_float(va[e]);
-                        if (n0 + 32 + e < p.P) dst[(size_t)(n0 + 32 + e) * p.Kp] = __uint_as_float(vb[e]);
-                    }
+                for (int e = 0; e < 32; ++e) {
+                    if (n0 + e < p.P) dst[(size_t)(n0 + e) * p.Kp] = __uint_as_float(va[e]);
+                    if (n0 + 32 + e < p.P) dst[(size_t)(n0 + 32 + e) * p.Kp] = __uint_as_float(vb[e]);
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bars[SB_TEMPTY]);
+            if (lane == 0) mbar_arrive(&bars[EB_TEMPTY]);
         }
     }
     tc_fence_before();
     __syncthreads();
+    if (p.S > 1) cluster_sync();   // no remote access into a CTA that has exited
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, p.tmem_cols);
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -649,57 +630,92 @@ cudaError_t get_encoder() {
 }
 
 // 2D bf16 tensor map: `cols` x `rows` with row pitch `pitch_elems`, box
-// 16 x box_rows with the 32-byte swizzle, or 64 x box_rows with the 128-byte
-// swizzle when wide; zero fill out of bounds.
-bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t pitch_elems, uint32_t box_rows,
-              bool wide = false) {
+// 16 x box_rows with the 32-byte swizzle; zero fill out of bounds.
+bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t pitch_elems, uint32_t box_rows) {
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {pitch_elems * 2};
-    cuuint32_t box[2] = {wide ? 64u : 16u, box_rows};
+    cuuint32_t box[2] = {16u, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, wide ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-uint32_t pow2_cols(int n) {
-    uint32_t c = 32;
-    while ((int)c < n) c <<= 1;
-    return c;
-}
-
-struct BfCfg {
-    int split, ncta, nstage, sc, ny;
-    size_t post_smem, stat_smem;
+struct EncCfg {
+    int nkb, S, nstage, nslot, ny;
+    size_t smem;
 };
 
-bool bf16_config(const fv_gmm *g, BfCfg &c) {
-    const int nkb = round_up(g->D, 16) / 16;
-    c.split = g->Kp > 256 ? 2 : 1;
-    c.ncta = g->Kp / c.split;
-    c.nstage = 2;
-    int maxsmem = 232448;
-    if (post_smem(nkb, c.ncta, 2, c.split).total > (uint32_t)maxsmem) c.nstage = 1;
-    c.post_smem = post_smem(nkb, c.ncta, c.nstage, c.split).total;
-    c.sc = (g->Kp % 256 == 0) ? 256 : 128;
-    c.ny = 3 * nkb * 16 + 16;
-    c.stat_smem = stat_smem(nkb, c.sc).total;
-    return c.post_smem <= (size_t)maxsmem && c.stat_smem <= (size_t)maxsmem && c.ncta % 64 == 0 && c.ncta <= 256 &&
-           c.ny <= 256;
+bool enc_config(const fv_gmm *g, EncCfg &c) {
+    c.nkb = round_up(g->D, 16) / 16;
+    c.S = g->Kp / kComps;
+    c.ny = 3 * c.nkb * 16 + 16;
+    // prefer two Y stages, then four exchange slots
+    c.nstage = 1;
+    c.nslot = 2;
+    if (enc_smem(c.nkb, c.S, 2, 4).total <= (uint32_t)kMaxSmem) {
+        c.nstage = 2;
+        c.nslot = 4;
+    } else if (enc_smem(c.nkb, c.S, 2, 2).total <= (uint32_t)kMaxSmem) {
+        c.nstage = 2;
+    } else if (enc_smem(c.nkb, c.S, 1, 4).total <= (uint32_t)kMaxSmem) {
+        c.nslot = 4;
+    }
+    c.smem = enc_smem(c.nkb, c.S, c.nstage, c.nslot).total;
+    return g->Kp % kComps == 0 && c.S >= 1 && c.S <= 4 && c.ny <= 256 && c.smem <= (size_t)kMaxSmem;
+}
+
+void enc_launch_config(const EncCfg &c, int clusters, cudaStream_t st, cudaLaunchConfig_t &cfg,
+                       cudaLaunchAttribute *attr) {
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3((unsigned)(clusters * c.S));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = c.smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c.S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
 }
 
 }  // namespace
 
-int bf16_stat_ctas(const fv_gmm *g, int64_t rows, int sms) {
-    // one persistent CTA per SM per component group, each with at least 512
-    // rows (a slot is K x (3D+1) floats; shorter shares would move more slot
-    // bytes than posterior bytes)
-    const int sc = (g->Kp % 256 == 0) ? 256 : 128;
-    const int groups = g->Kp / sc;
-    const int per_group = std::max(1, sms / groups);
-    const int64_t by_rows = std::max<int64_t>(1, rows / 512);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(per_group, by_rows));
+int bf16_max_shares(const fv_gmm *g, int sms) {
+    // clusters of the encoder kernel resident at once (one CTA per SM; a
+    // cluster's CTAs share a GPC, so larger clusters leave some SMs idle)
+    EncCfg c;
+    if (!enc_config(g, c)) return 1;
+    if (c.S == 1) return std::max(1, sms);
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, c.S, c.smem);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    enc_launch_config(c, std::max(1, sms / c.S), nullptr, cfg, attr);
+    if (cudaFuncSetAttribute(bf16_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&n, bf16_encode_kernel, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = std::max(1, sms / c.S);
+    }
+    cache[key] = n;
+    return n;
+}
+
+int bf16_shares(const fv_gmm *g, int64_t rows, int sms) {
+    // persistent clusters over balanced row shares; a share of fewer than two
+    // tiles would move more slot bytes than it saves time
+    const int64_t tiles = (rows + kRows - 1) / kRows;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(bf16_max_shares(g, sms), (tiles + 1) / 2));
 }
 
 cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, uint16_t *Xb, cudaStream_t st) {
@@ -713,81 +729,43 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
     return cudaGetLastError();
 }
 
-int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
-                     const StatUnit *units, const int2 *cta_units, int n_ctas, float *part, int P, int sms,
-                     uint32_t *err, cudaStream_t st, const int64_t *rows_dev) {
-    if (rows <= 0 || n_ctas <= 0) return FV_OK;
+int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, const StatUnit *units,
+                     const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st) {
+    if (rows <= 0 || n_shares <= 0) return FV_OK;
     if (get_encoder() != cudaSuccess) return fail(FV_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
-    BfCfg c;
-    if (!bf16_config(g, c)) return fail(FV_ERR_UNSUPPORTED, "BF16 form: shape does not fit the kernels' shared memory");
-    const int nkb = round_up(g->D, 16) / 16;
+    EncCfg c;
+    if (!enc_config(g, c)) return fail(FV_ERR_UNSUPPORTED, "BF16 form: shape does not fit the kernel's shared memory");
+    if (P != 3 * c.nkb * 16 + 1) return fail(FV_ERR_INVALID, "BF16 form: slot width mismatch");
     if (rows > (int64_t)INT32_MAX - 256) return fail(FV_ERR_UNSUPPORTED, "BF16 form: too many rows for one call");
 
-    CUtensorMap tmX128, tmX64, tmB, tmG;
-    if (!make_map(&tmX128, Xb, (uint64_t)g->D, (uint64_t)rows, (uint64_t)ldx, kTileRows) ||
-        !make_map(&tmX64, Xb, (uint64_t)g->D, (uint64_t)rows, (uint64_t)ldx, kStatRows) ||
-        !make_map(&tmB, g->dev.bimg, (uint64_t)nkb * 16, (uint64_t)4 * g->Kp, (uint64_t)nkb * 16, (uint32_t)c.ncta) ||
-        !make_map(&tmG, gamma, (uint64_t)g->Kp, (uint64_t)rows, (uint64_t)g->Kp, kStatRows, true))
+    CUtensorMap tmX, tmB;
+    if (!make_map(&tmX, Xb, (uint64_t)g->D, (uint64_t)rows, (uint64_t)ldx, kRows) ||
+        !make_map(&tmB, g->dev.bimg, (uint64_t)c.nkb * 16, (uint64_t)4 * g->Kp, (uint64_t)c.nkb * 16, kComps))
         return fail(FV_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 
-    // posteriors: persistent clusters over 128-row tiles
-    PostArgs pa;
-    pa.rows = rows;
-    pa.ntiles = (int)((rows + kTileRows - 1) / kTileRows);
-    pa.rows_dev = rows_dev;   // rows is then the buffers' capacity
-    pa.nkb = nkb;
-    pa.Kp = g->Kp;
-    pa.ncta = c.ncta;
-    pa.split = c.split;
-    pa.nstage = c.nstage;
-    pa.tmem_cols = pow2_cols(2 * c.ncta);
-    pa.cl2 = g->dev.cl2;
-    pa.gamma = gamma;
-    pa.err = err;
-    cudaError_t e = cudaFuncSetAttribute(bf16_posteriors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)c.post_smem);
-    if (e != cudaSuccess) return cuda_fail(e, "bf16 posteriors: smem attribute");
-    const int nclusters = rows_dev ? std::max(1, sms / c.split) : std::max(1, std::min(pa.ntiles, sms / c.split));
-    cudaLaunchConfig_t cfg = {};
+    EncArgs a;
+    a.nkb = c.nkb;
+    a.Kp = g->Kp;
+    a.S = c.S;
+    a.nstage = c.nstage;
+    a.nslot = c.nslot;
+    a.ny = c.ny;
+    a.P = P;
+    a.cl2 = g->dev.cl2;
+    a.units = units;
+    a.cl_units = cl_units;
+    a.part = part;
+    a.err = err;
+    cudaError_t e = cudaFuncSetAttribute(bf16_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "bf16 encoder: smem attribute");
+    cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)(nclusters * c.split));
-    cfg.blockDim = dim3(kPostThreads);
-    cfg.dynamicSmemBytes = c.post_smem;
-    cfg.stream = st;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)c.split;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    enc_launch_config(c, n_shares, st, cfg, attr);
     {
-        KernelTimer kt_("bf16_posteriors", st);
-        e = cudaLaunchKernelEx(&cfg, bf16_posteriors_kernel, tmX128, tmB, pa);
+        KernelTimer kt_("bf16_encode", st);
+        e = cudaLaunchKernelEx(&cfg, bf16_encode_kernel, tmX, tmB, a);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "bf16 posteriors launch");
-
-    // statistics: persistent CTAs over balanced row shares x component groups
-    StatArgs sa;
-    sa.nkb = nkb;
-    sa.D = g->D;
-    sa.Kp = g->Kp;
-    sa.sc = c.sc;
-    sa.ny = c.ny;
-    sa.P = P;
-    sa.tmem_cols = pow2_cols((c.sc / 128) * c.ny);
-    sa.units = units;
-    sa.cta_units = cta_units;
-    sa.part = part;
-    sa.err = err;
-    e = cudaFuncSetAttribute(bf16_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.stat_smem);
-    if (e != cudaSuccess) return cuda_fail(e, "bf16 statistics: smem attribute");
-    dim3 grid((unsigned)n_ctas, (unsigned)(g->Kp / c.sc));
-    {
-        KernelTimer kt_("bf16_stats", st);
-        bf16_stats_kernel<<<grid, kThreads, c.stat_smem, st>>>(tmG, tmX64, sa);
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "bf16 statistics launch");
+    if (e != cudaSuccess) return cuda_fail(e, "bf16 encoder launch");
     return FV_OK;
 }
 

@@ -5,20 +5,22 @@
 
 namespace fv {
 
-// Number of persistent statistics CTAs (row shares) for `rows` packed rows.
-int bf16_stat_ctas(const fv_gmm *g, int64_t rows, int sms);
+// Clusters of the fused encoder kernel resident at once on the current device.
+int bf16_max_shares(const fv_gmm *g, int sms);
+
+// Number of row shares (persistent clusters) for a call over `rows` packed rows.
+int bf16_shares(const fv_gmm *g, int64_t rows, int sms);
 
 // FP32 descriptors (rows x D) -> bfloat16 rows of pitch Dp (zero padded).
 cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, uint16_t *Xb, cudaStream_t st);
 
-// Posteriors and statistics of the BF16 form; returns an fv_status.
+// Posteriors and statistics of the BF16 form in one kernel; returns an fv_status.
+// Xb: bf16 rows of pitch ldx; rows: rows addressable in Xb (rows past it read as zero).
+// units: row ranges (one frame each) grouped per share; cl_units[c] = (first
+// unit, count) of share c, which one cluster of the kernel walks.
+// part: [slot][P][Kp] statistics slots, P = 3*D16 + 1.
 // err: device word a kernel sets when a bounded wait gives up (zeroed by the caller).
-// units: row segments (one frame each) grouped per statistics CTA;
-// cta_units[c] = (first unit, count) of CTA c.
-// rows_dev (nullable): device row count read by the kernels at start; rows is
-// then the capacity of Xb/gamma (graph replays with a varying row count).
-int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, uint16_t *gamma,
-                     const StatUnit *units, const int2 *cta_units, int n_ctas, float *part, int P, int sms,
-                     uint32_t *err, cudaStream_t st, const int64_t *rows_dev = nullptr);
+int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, const StatUnit *units,
+                     const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st);
 
 }  // namespace fv

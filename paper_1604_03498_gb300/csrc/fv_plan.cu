@@ -2,10 +2,11 @@
 // statistics grid, and one CUDA graph of the kernel sequence per plan.
 //
 // The graph is captured once against the plan's buffers: bf16 input rows,
-// posteriors, statistics slots, a device work list and the output vectors.
-// The kernels take the batch's row count and frame count from the work-list
-// header in device memory, and the persistent kernels' grids do not depend on
-// the batch, so one capture serves every batch up to the plan's capacity. A
+// statistics slots, a device work list and the output vectors. The encoder
+// walks the batch's units from the device work list and the finalise takes
+// the frame count from its header, and the persistent encoder's grid does not
+// depend on the batch, so one capture serves every batch up to the plan's
+// capacity. A
 // run builds the balanced work list on the host, uploads it (one copy from a
 // pinned staging slot) and launches the graph on the caller's stream.
 #include <cstdio>
@@ -22,7 +23,7 @@
 namespace fv {
 namespace {
 
-constexpr int kGraphKernels = 4;   // posteriors, statistics, finalise A, finalise B
+constexpr int kGraphKernels = 3;   // fused encoder, finalise A, finalise B
 
 struct WorkHeader {
     int64_t rows;
@@ -80,11 +81,11 @@ using namespace fv;
 
 struct fv_batch_plan {
     const fv_gmm *g = nullptr;
-    int device = 0, sms = 1, groups = 1, G = 1, Gmax = 1, P = 0, max_frames = 0, max_units = 0;
+    int device = 0, sms = 1, base = 1, G = 1, Gmax = 1, P = 0, max_frames = 0, max_units = 0;
     int64_t max_rows = 0;
     fv_batch_plan_info info{};
     char *block = nullptr;
-    uint16_t *xin = nullptr, *gamma = nullptr;
+    uint16_t *xin = nullptr;
     float *part = nullptr, *out = nullptr;
     double *sq = nullptr;
     uint32_t *err = nullptr;
@@ -128,10 +129,9 @@ int launch_sequence(fv_batch_plan *p, int G, cudaStream_t st) {
     const fv_gmm *g = p->g;
     cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "batch plan: error word");
-    const int64_t *rows_dev = (const int64_t *)p->wl;
     const int *B_dev = (const int *)(p->wl + 8);
-    int rc = run_bf16_encoder(g, p->xin, g->Dp, p->max_rows, p->gamma, (const StatUnit *)(p->wl + p->off_units),
-                              (const int2 *)(p->wl + p->off_cta), G, p->part, p->P, p->sms, p->err, st, rows_dev);
+    int rc = run_bf16_encoder(g, p->xin, g->Dp, p->max_rows, (const StatUnit *)(p->wl + p->off_units),
+                              (const int2 *)(p->wl + p->off_cta), G, p->part, p->P, p->err, st);
     if (rc != FV_OK) return rc;
     if ((e = launch_finalize(g, p->part, p->P, true, (const FrameInfo *)(p->wl + p->off_frames), p->max_frames, p->sq,
                              p->out, st, p->err, B_dev)) != cudaSuccess)
@@ -153,7 +153,7 @@ int autotune(fv_batch_plan *p, cudaStream_t st, double *best_ms) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const int base = std::max(1, p->sms / p->groups);
+    const int base = p->base;
     int bestG = base;
     *best_ms = 1e30;
     for (int f = 1; f <= 3; ++f) {
@@ -222,19 +222,18 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
     p->g = gmm;
     p->device = dev;
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
-    p->groups = (gmm->Kp % 256 == 0) ? gmm->Kp / 256 : gmm->Kp / 128;
+    p->base = bf16_max_shares(gmm, p->sms);
     p->max_frames = cfg->max_frames;
     p->max_rows = cfg->max_rows;
     p->P = 3 * gmm->Dp + 1;
-    p->Gmax = 3 * std::max(1, p->sms / p->groups);
-    p->G = std::max(1, p->sms / p->groups);
+    p->Gmax = 3 * p->base;
+    p->G = p->base;
     p->max_units = p->Gmax + p->max_frames;
 
     const int Kp = gmm->Kp, Dp = gmm->Dp;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 1023) / 1024 * 1024; return o; };
     const size_t o_x = take(sizeof(uint16_t) * (size_t)p->max_rows * Dp);
-    const size_t o_g = take(sizeof(uint16_t) * (size_t)p->max_rows * Kp);
     const size_t o_part = take(sizeof(float) * (size_t)p->max_units * Kp * p->P);
     const size_t o_sq = take(sizeof(double) * (size_t)p->max_frames * (Kp / 32) * ((gmm->D + 7) / 8));
     const size_t o_out = take(sizeof(float) * (size_t)p->max_frames * 2 * gmm->K * gmm->D);
@@ -251,7 +250,6 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
         return fail(FV_ERR_OOM, std::string("fv_batch_plan_create: cudaMalloc: ") + cudaGetErrorString(e));
     }
     p->xin = (uint16_t *)(p->block + o_x);
-    p->gamma = (uint16_t *)(p->block + o_g);
     p->part = (float *)(p->block + o_part);
     p->sq = (double *)(p->block + o_sq);
     p->out = (float *)(p->block + o_out);
@@ -271,8 +269,8 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
     }
     int rc = FV_OK;
     do {
-        // finite contents everywhere: rows past a batch are read (and masked) by
-        // the statistics stages, and 0 * NaN would not be 0
+        // defined contents everywhere: rows past a unit are read (and zeroed)
+        // by the encoder's tiles
         if ((e = cudaMemsetAsync(p->block, 0, off, st)) != cudaSuccess) {
             rc = cuda_fail(e, "fv_batch_plan_create: clear");
             break;

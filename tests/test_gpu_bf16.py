@@ -7,10 +7,10 @@ input); the tolerance is 2e-3 max-abs on the normalised Fisher vector. The
 full-size cases also check the error against the oracle on the original FP32
 descriptors (input quantisation included) against the same bound.
 
-Shapes span several 128-row posterior tiles with ragged tails, statistics
-ranges ending inside a 64-row stage, K padded to 128, a 2-CTA component
-split (K > 256) with a non-256 per-CTA width, D not a multiple of 16, and
-the degenerate N = 1 / K = 1 cases."""
+Shapes span several 128-row tiles with ragged tails, frame ranges ending
+inside a tile, K padded to 128, clusters of 1 to 4 CTAs (128 components
+each, posteriors normalised across the cluster), D not a multiple of 16, a
+single Y stage (D=80 with K=512), and the degenerate N = 1 / K = 1 cases."""
 import numpy as np
 import pytest
 
@@ -26,12 +26,12 @@ def _rounded(X):
 
 
 @pytest.mark.parametrize("K,D,N,seed", [
-    (64, 64, 1000, 1),      # Kp=128, one component chunk
-    (256, 64, 777, 2),      # resident B at K=256, ragged
+    (64, 64, 1000, 1),      # Kp=128: one CTA per cluster
+    (256, 64, 777, 2),      # 2-CTA clusters, ragged last tile
     (130, 17, 333, 3),      # padded K and D
-    (300, 32, 1290, 4),     # Kp=384: 2-CTA split, 192 components per CTA
-    (512, 64, 2000, 5),     # 2-CTA split, single A stage
-    (256, 80, 513, 6),      # D=80: five 16-column blocks, single A stage
+    (300, 32, 1290, 4),     # Kp=384: 3-CTA clusters
+    (512, 64, 2000, 5),     # 4-CTA clusters
+    (256, 80, 513, 6),      # D=80: five 16-column blocks
     (1, 16, 5, 7),
     (64, 64, 1, 8),
 ])
@@ -75,8 +75,11 @@ def test_bf16_raw_entry_matches_fp32_input_entry():
     assert max_err(out_raw.cpu().numpy()[0], out_f32.cpu().numpy()) <= 1e-6
 
 
-def test_bf16_batch_matches_single_frames():
-    K, D = 256, 64
+@pytest.mark.parametrize("K,D", [(256, 64), (512, 80)])
+def test_bf16_batch_matches_single_frames(K, D):
+    """Frames of mixed sizes in one call: units start and end inside tiles,
+    shares hold several units (several statistics write-outs per cluster);
+    K=512, D=80 runs 4-CTA clusters with a single Y stage."""
     _, w, mu, var = case(K, D, 10, 31)
     frames = [synth.sample_descriptors(w, mu, var, n, seed=300 + i, gmm_frac=0.8)
               for i, n in enumerate([5000, 1, 0, 129, 12000])]
