@@ -326,7 +326,9 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
             rc = run_bf16_encoder(g, xb, ldx_dev, rows, und, ctad, nctas, part, P, errd, st);
             if (rc != FV_OK) break;
         }
-        if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd)) != cudaSuccess) {
+        int max_slots = 1;
+        for (const FrameInfo &fi : plan.frames) max_slots = std::max(max_slots, fi.nslots);
+        if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd, nullptr, max_slots)) != cudaSuccess) {
             rc = cuda_fail(e, "finalise launch");
             break;
         }

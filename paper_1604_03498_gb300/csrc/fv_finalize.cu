@@ -4,13 +4,19 @@
 // v = V/(N sqrt(2w)), signed square root, L2.
 //
 // Slots are component-fastest: part[slot][j][Kp], j indexing the statistic.
-// Kernel A: one block per (32 components x 8 dimensions, frame); each thread
-// sums the frame's slots for its (component, dimension) in slot order (fixed,
-// so a frame's vector does not depend on what else was encoded with it),
-// forms u and v, takes sign(z) sqrt|z|, and the block writes its [32][8]
-// tiles through shared memory (runs of 8 contiguous floats); the block's sum
-// of squares goes to sq. Kernel B: one block per frame sums the block squares
-// (fixed-order tree) and scales the frame's vector by 1/||z||.
+// Kernel R adds the frame's slots into its first slot in one canonical order:
+// eight partial sums p_g over the slots s = g (mod 8) in increasing s, then
+// p_0 + p_1 + ... + p_7 left to right. The order depends on nothing but the
+// frame's own slots, so a frame's vector does not depend on what else was
+// encoded with it. A block covers 32 components of one frame: with many
+// slots, eight warps take one residue each for one statistic; with a few,
+// each of eight warps takes a statistic and keeps the eight partials itself. Kernel A: one
+// block per (32 components x 8 dimensions, frame) reads the totals, forms u
+// and v, takes sign(z) sqrt|z|, and writes its [32][8] tiles through shared
+// memory (runs of 8 contiguous floats); the block's sum of squares goes to
+// sq. Kernel B: blocks of 1024 output values per frame each add the frame's
+// block squares (the same fixed-order tree in every block) and scale their
+// values by 1/||z||.
 //
 // All per-element arithmetic is FP32 (GB300's FP64 rate is a small fraction
 // of its FP32 rate). The BF16 form's raw moments are centred with FMAs whose
@@ -28,23 +34,62 @@ namespace fv {
 namespace {
 
 constexpr int FA_THREADS = 256;   // 32 components x 8 dimension lanes
-constexpr int FB_THREADS = 256;
+constexpr int FB_THREADS = 256;   // one float4 each
 
 __device__ __forceinline__ float ssqrtf(float v) { return v > 0.f ? sqrtf(v) : (v < 0.f ? -sqrtf(-v) : 0.f); }
 
-// Sum of one statistic over a frame's slots in a fixed order; four
-// interleaved partial sums keep four loads in flight.
-__device__ __forceinline__ float slot_sum(const float *p, size_t stride, int n) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    int s = 0;
-    for (; s + 4 <= n; s += 4) {
-        a0 += p[(size_t)s * stride];
-        a1 += p[(size_t)(s + 1) * stride];
-        a2 += p[(size_t)(s + 2) * stride];
-        a3 += p[(size_t)(s + 3) * stride];
+// grid (ceil(P/J), Kp/32, frames), block 256: frame totals into the frame's
+// first slot. split = true: J = 1, warp w sums residue w; split = false:
+// J = 8, warp w sums statistic blockIdx.x * 8 + w over all residues.
+__global__ void __launch_bounds__(256)
+finalize_r_kernel(float *__restrict__ part, int P, int Kp, bool split, const FrameInfo *__restrict__ frames,
+                  const int *__restrict__ B_dev) {
+    __shared__ float red[8][32];
+    const int f = blockIdx.z;
+    if (B_dev && f >= *B_dev) return;
+    const FrameInfo fr = frames[f];
+    if (fr.n <= 0 || fr.nslots <= 1) return;   // nothing to add
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = fr.nslots;
+    const size_t sstride = (size_t)P * Kp;
+    if (split) {
+        float *p = part + (size_t)fr.slot0 * sstride + (size_t)blockIdx.x * Kp + blockIdx.y * 32 + lane;
+        float a = 0.f;
+#pragma unroll 4
+        for (int s = w; s < n; s += 8) a += p[(size_t)s * sstride];
+        red[w][lane] = a;
+        __syncthreads();
+        if (w == 0) {
+            float t = red[0][lane];
+#pragma unroll
+            for (int g = 1; g < 8; ++g) t += red[g][lane];
+            p[0] = t;
+        }
+        return;
     }
-    for (; s < n; ++s) a0 += p[(size_t)s * stride];
-    return (a0 + a1) + (a2 + a3);
+    const int j = blockIdx.x * 8 + w;
+    if (j >= P) return;
+    float *p = part + (size_t)fr.slot0 * sstride + (size_t)j * Kp + blockIdx.y * 32 + lane;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f, a7 = 0.f;
+    int s = 0;
+    for (; s + 8 <= n; s += 8) {
+        a0 += p[(size_t)(s + 0) * sstride];
+        a1 += p[(size_t)(s + 1) * sstride];
+        a2 += p[(size_t)(s + 2) * sstride];
+        a3 += p[(size_t)(s + 3) * sstride];
+        a4 += p[(size_t)(s + 4) * sstride];
+        a5 += p[(size_t)(s + 5) * sstride];
+        a6 += p[(size_t)(s + 6) * sstride];
+        a7 += p[(size_t)(s + 7) * sstride];
+    }
+    if (s + 0 < n) a0 += p[(size_t)(s + 0) * sstride];
+    if (s + 1 < n) a1 += p[(size_t)(s + 1) * sstride];
+    if (s + 2 < n) a2 += p[(size_t)(s + 2) * sstride];
+    if (s + 3 < n) a3 += p[(size_t)(s + 3) * sstride];
+    if (s + 4 < n) a4 += p[(size_t)(s + 4) * sstride];
+    if (s + 5 < n) a5 += p[(size_t)(s + 5) * sstride];
+    if (s + 6 < n) a6 += p[(size_t)(s + 6) * sstride];
+    p[0] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
 // grid (Kp/32, ceil(D/8), frames); thread (lane -> component, grp -> dimension)
@@ -66,17 +111,17 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
 
     float zu = 0.f, zv = 0.f;
     if (d < D && k < K && fr.n > 0) {
-        const float *ps = part + (size_t)fr.slot0 * sstride + k;
-        const float S0 = slot_sum(ps + (size_t)(P - 1) * Kp, sstride, fr.nslots);
+        const float *ps = part + (size_t)fr.slot0 * sstride + k;   // the frame totals
+        const float S0 = ps[(size_t)(P - 1) * Kp];
         const int jb = RAW ? (P - 1) / 3 : D;   // statistic block width (D16 for BF16 slots)
-        const float s1 = slot_sum(ps + (size_t)d * Kp, sstride, fr.nslots);
-        const float s2 = slot_sum(ps + (size_t)(jb + d) * Kp, sstride, fr.nslots);
+        const float s1 = ps[(size_t)d * Kp];
+        const float s2 = ps[(size_t)(jb + d) * Kp];
         const float inv_n = 1.0f / (float)fr.n;
         const float al = g.alpha[k] * inv_n, be = g.beta[k] * inv_n;
         const float isd = g.s_t[(size_t)d * Kp + k], pr = g.prec_t[(size_t)d * Kp + k];
         float u, v;
         if (RAW) {
-            const float s3 = slot_sum(ps + (size_t)(2 * jb + d) * Kp, sstride, fr.nslots);
+            const float s3 = ps[(size_t)(2 * jb + d) * Kp];
             const float m = g.mu_t[(size_t)d * Kp + k];
             const float a = fmaf(-m, S0, s1);
             const float b = fmaf(-m, s1, s2) + s3;
@@ -110,11 +155,12 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
     if (threadIdx.x == 0) sq[((size_t)f * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (double)red[0];
 }
 
+// grid (ceil(2KD / 1024), frames)
 __global__ void __launch_bounds__(FB_THREADS)
 finalize_b_kernel(int K, int D, int nb, const double *__restrict__ sq, float *__restrict__ out,
                   const uint32_t *__restrict__ err, const int *__restrict__ B_dev) {
     __shared__ float red[FB_THREADS];
-    const int f = blockIdx.x;
+    const int f = blockIdx.y;
     if (B_dev && f >= *B_dev) return;
     // fixed-order FP32 tree over the frame's block sums (no FP64 on the hot path)
     float t = 0.f;
@@ -128,32 +174,43 @@ finalize_b_kernel(int K, int D, int nb, const double *__restrict__ sq, float *__
     const float tot = red[0];
     const size_t n = (size_t)2 * K * D;
     float *o = out + (size_t)f * n;
+    const size_t j0 = (size_t)blockIdx.x * FB_THREADS * 4 + threadIdx.x * 4;
+    if (j0 >= n) return;
+    const size_t j1 = j0 + 4 < n ? j0 + 4 : n;
     if (err && *err) {   // an earlier kernel of this call gave up: poison the output
-        for (size_t j = threadIdx.x; j < n; j += FB_THREADS) o[j] = __int_as_float(0x7fc00000);
+        for (size_t j = j0; j < j1; ++j) o[j] = __int_as_float(0x7fc00000);
         return;
     }
     if (!(tot > 0.f)) return;   // all-zero vector stays zero
     const float inv = rsqrtf(tot);
-    if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
-        float4 *o4 = reinterpret_cast<float4 *>(o);
-        for (size_t j = threadIdx.x; j < n / 4; j += FB_THREADS) {
-            float4 v = o4[j];
-            v.x *= inv;
-            v.y *= inv;
-            v.z *= inv;
-            v.w *= inv;
-            o4[j] = v;
-        }
+    if (j1 == j0 + 4 && (reinterpret_cast<uintptr_t>(o + j0) & 15) == 0) {
+        float4 v = *reinterpret_cast<float4 *>(o + j0);
+        v.x *= inv;
+        v.y *= inv;
+        v.z *= inv;
+        v.w *= inv;
+        *reinterpret_cast<float4 *>(o + j0) = v;
     } else {
-        for (size_t j = threadIdx.x; j < n; j += FB_THREADS) o[j] *= inv;
+        for (size_t j = j0; j < j1; ++j) o[j] *= inv;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments, const FrameInfo *frames,
-                            int B, double *sq, float *out, cudaStream_t st, const uint32_t *err, const int *B_dev) {
+cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments, const FrameInfo *frames,
+                            int B, double *sq, float *out, cudaStream_t st, const uint32_t *err, const int *B_dev,
+                            int max_slots) {
     if (B <= 0) return cudaSuccess;
+    {
+        // the split only changes which warps do the work, not the order
+        const bool split = max_slots >= 16;
+        const int J = split ? 1 : 8;
+        KernelTimer kt_("finalize_r", st);
+        finalize_r_kernel<<<dim3((unsigned)((P + J - 1) / J), (unsigned)(g->Kp / 32), (unsigned)B), 256, 0, st>>>(
+            part, P, g->Kp, split, frames, B_dev);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const int nbx = g->Kp / 32, nby = (g->D + 7) / 8, nb = nbx * nby;
     dim3 grid_a((unsigned)nbx, (unsigned)nby, (unsigned)B);
     if (raw_moments) {
@@ -165,11 +222,13 @@ cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_
         finalize_a_kernel<false><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out,
                                                                  B_dev);
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     {
         KernelTimer kt_("finalize_b", st);
-        finalize_b_kernel<<<(unsigned)B, FB_THREADS, 0, st>>>(g->K, g->D, nb, sq, out, err, B_dev);
+        const size_t n = (size_t)2 * g->K * g->D;
+        const unsigned nbb = (unsigned)((n + FB_THREADS * 4 - 1) / (FB_THREADS * 4));
+        finalize_b_kernel<<<dim3(nbb, (unsigned)B), FB_THREADS, 0, st>>>(g->K, g->D, nb, sq, out, err, B_dev);
     }
     return cudaGetLastError();
 }

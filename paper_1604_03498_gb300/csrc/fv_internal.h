@@ -118,11 +118,14 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 // L2. raw_moments selects the BF16 form's [S1, S2hi, S2lo, S0] layout
 // (blocks of D16 = D rounded up to 16, P = 3*D16+1) over the FP32 form's
 // centred [A, B, S0] layout (blocks of D, P = 2D+1).
-// sq needs B * (Kp / 32) * ceil(D / 8) doubles.
+// sq needs B * (Kp / 32) * ceil(D / 8) doubles. Each frame's first slot is
+// overwritten with the frame's totals (three launches: slot reduction,
+// encode, normalise). max_slots: the most slots a frame has (any value is
+// correct; it picks the reduction's split).
 // err (nullable): device error word of the call; when a kernel set it, every
 // output element becomes NaN so a failed encode can never look valid.
-cudaError_t launch_finalize(const fv_gmm *g, const float *part, int P, bool raw_moments,
+cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments,
                             const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
-                            const uint32_t *err = nullptr, const int *B_dev = nullptr);
+                            const uint32_t *err = nullptr, const int *B_dev = nullptr, int max_slots = 1);
 
 }  // namespace fv

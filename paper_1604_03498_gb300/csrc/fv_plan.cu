@@ -23,7 +23,7 @@
 namespace fv {
 namespace {
 
-constexpr int kGraphKernels = 3;   // fused encoder, finalise A, finalise B
+constexpr int kGraphKernels = 4;   // fused encoder, finalise R, A and B
 
 struct WorkHeader {
     int64_t rows;
