@@ -4,7 +4,8 @@
 //   l_ik = c'_k - 1/2 sum_d t_ikd^2,  t_ikd = x_id/sigma_kd - mu_kd/sigma_kd
 //   gamma_ik = exp(l_ik - max_k l_ik) / sum_k exp(l_ik - max_k l_ik)
 // computed for a 64-row block against every component with register tiles of
-// 8 rows x CPL components per thread (t is one FMA, t^2 accumulation another),
+// 8 rows x CPL components per thread (t is one FMA, t^2 accumulation another,
+// both on component pairs with packed f32x2 instructions),
 // the row block's log-likelihoods kept in shared memory for the softmax.
 //
 // Statistics (Algorithm 1 second loop; the paper's Phase 2, Algorithm 3 with
@@ -12,7 +13,7 @@
 // 64-component chunk and accumulates, per (k, d) held in registers,
 //   A_kd += gamma_ik (x_id - mu_kd),  B_kd += gamma_ik (x_id - mu_kd)^2,
 //   S0_k += gamma_ik
-// and the finalise kernel forms U = A/sigma and V = B/sigma^2 - S0 in FP64.
+// and the finalise kernel forms U = A/sigma and V = B/sigma^2 - S0.
 // The residual x - mu carries a rounding error relative to itself; the
 // posteriors' single-FMA form x/sigma - mu/sigma errs by ~eps |mu/sigma|, which
 // is harmless inside a softmax but would be amplified near zero by the signed
@@ -24,6 +25,30 @@
 namespace fv {
 
 namespace {
+
+// Packed FP32 pairs (f32x2: two lanes per instruction, same rounding as the
+// scalar operations; halves the instruction count of the inner loops).
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(uint64_t r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
 
 constexpr int P_BM = 64;   // rows per posterior block
 constexpr int P_DS = 32;   // dimension slice staged in shared memory
@@ -50,11 +75,11 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
     const int64_t row0 = (int64_t)blockIdx.x * P_BM;
 
     for (int kc0 = 0; kc0 < Kp; kc0 += KC) {
-        float acc[8][CPL];
+        uint64_t acc[8][CPL / 2];   // component pairs
 #pragma unroll
         for (int r = 0; r < 8; ++r)
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) acc[r][c] = 0.f;
+            for (int c = 0; c < CPL / 2; ++c) acc[r][c] = 0ull;
 
         for (int d0 = 0; d0 < D; d0 += P_DS) {
             __syncthreads();
@@ -87,21 +112,34 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
                     sv[0] = a.x; sv[1] = a.y;
                     nv[0] = b.x; nv[1] = b.y;
                 }
+                uint64_t s2[CPL / 2], n2[CPL / 2];
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
+                for (int c = 0; c < CPL / 2; ++c) {
+                    s2[c] = pk2(sv[2 * c], sv[2 * c + 1]);
+                    n2[c] = pk2(nv[2 * c], nv[2 * c + 1]);
+                }
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) {
-                        const float t = fmaf(xv[r], sv[c], nv[c]);
-                        acc[r][c] = fmaf(t, t, acc[r][c]);
+                for (int r = 0; r < 8; ++r) {
+                    const uint64_t x2 = pk2(xv[r], xv[r]);
+#pragma unroll
+                    for (int c = 0; c < CPL / 2; ++c) {
+                        const uint64_t t = fma2(x2, s2[c], n2[c]);
+                        acc[r][c] = fma2(t, t, acc[r][c]);
                     }
+                }
             }
         }
         // l = c' - dist/2 for this chunk
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const float ck = cst[kc0 + lane * CPL + c];
+        for (int c = 0; c < CPL / 2; ++c) {
+            const float ck0 = cst[kc0 + lane * CPL + 2 * c], ck1 = cst[kc0 + lane * CPL + 2 * c + 1];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + c] = fmaf(-0.5f, acc[r][c], ck);
+            for (int r = 0; r < 8; ++r) {
+                float a0, a1;
+                up2(acc[r][c], a0, a1);
+                sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c] = fmaf(-0.5f, a0, ck0);
+                sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c + 1] = fmaf(-0.5f, a1, ck1);
+            }
         }
     }
     __syncthreads();
@@ -157,15 +195,18 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     const int kb = kc0 + cg * S_CPT, dl = dg * S_DPT, db = dc0 + dl;
     const bool active = db < D;
 
-    float m[S_CPT][S_DPT], U[S_CPT][S_DPT], W[S_CPT][S_DPT], S0[S_CPT];
+    uint64_t nm[S_CPT][S_DPT / 2], U[S_CPT][S_DPT / 2], W[S_CPT][S_DPT / 2];
+    float S0[S_CPT];
 #pragma unroll
     for (int c = 0; c < S_CPT; ++c) {
         S0[c] = 0.f;
 #pragma unroll
-        for (int j = 0; j < S_DPT; ++j) {
-            m[c][j] = active ? mu_kd[(size_t)(kb + c) * Dp + db + j] : 0.f;
-            U[c][j] = 0.f;
-            W[c][j] = 0.f;
+        for (int j = 0; j < S_DPT / 2; ++j) {
+            const float m0 = active ? mu_kd[(size_t)(kb + c) * Dp + db + 2 * j] : 0.f;
+            const float m1 = active ? mu_kd[(size_t)(kb + c) * Dp + db + 2 * j + 1] : 0.f;
+            nm[c][j] = pk2(-m0, -m1);
+            U[c][j] = 0ull;
+            W[c][j] = 0ull;
         }
     }
 
@@ -205,16 +246,17 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
                 const float4 xa = *reinterpret_cast<const float4 *>(&Xs[r * S_DC + dl]);
                 const float4 xb = *reinterpret_cast<const float4 *>(&Xs[r * S_DC + dl + 4]);
                 const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-                const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                const uint64_t xv[4] = {pk2(xa.x, xa.y), pk2(xa.z, xa.w), pk2(xb.x, xb.y), pk2(xb.z, xb.w)};
 #pragma unroll
                 for (int c = 0; c < S_CPT; ++c) {
                     S0[c] += gv[c];
+                    const uint64_t g2 = pk2(gv[c], gv[c]);
 #pragma unroll
-                    for (int j = 0; j < S_DPT; ++j) {
-                        const float dx = xv[j] - m[c][j];
-                        const float gd = gv[c] * dx;
-                        U[c][j] += gd;
-                        W[c][j] = fmaf(gd, dx, W[c][j]);
+                    for (int j = 0; j < S_DPT / 2; ++j) {
+                        const uint64_t dx = add2(xv[j], nm[c][j]);
+                        const uint64_t gd = mul2(g2, dx);
+                        U[c][j] = add2(U[c][j], gd);
+                        W[c][j] = fma2(gd, dx, W[c][j]);
                     }
                 }
             }
@@ -227,11 +269,21 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     // slot layout part[slot][j][Kp]: this thread's 4 components are contiguous
     float *dst = part + (size_t)u.slot * Kp * P + kb;
 #pragma unroll
-    for (int j = 0; j < S_DPT; ++j) {
-        if (db + j < D) {
-            *reinterpret_cast<float4 *>(dst + (size_t)(db + j) * Kp) = make_float4(U[0][j], U[1][j], U[2][j], U[3][j]);
-            *reinterpret_cast<float4 *>(dst + (size_t)(D + db + j) * Kp) =
-                make_float4(W[0][j], W[1][j], W[2][j], W[3][j]);
+    for (int jp = 0; jp < S_DPT / 2; ++jp) {
+        float u0[S_CPT], u1[S_CPT], w0[S_CPT], w1[S_CPT];
+#pragma unroll
+        for (int c = 0; c < S_CPT; ++c) {
+            up2(U[c][jp], u0[c], u1[c]);
+            up2(W[c][jp], w0[c], w1[c]);
+        }
+        const int j = db + 2 * jp;
+        if (j < D) {
+            *reinterpret_cast<float4 *>(dst + (size_t)j * Kp) = make_float4(u0[0], u0[1], u0[2], u0[3]);
+            *reinterpret_cast<float4 *>(dst + (size_t)(D + j) * Kp) = make_float4(w0[0], w0[1], w0[2], w0[3]);
+        }
+        if (j + 1 < D) {
+            *reinterpret_cast<float4 *>(dst + (size_t)(j + 1) * Kp) = make_float4(u1[0], u1[1], u1[2], u1[3]);
+            *reinterpret_cast<float4 *>(dst + (size_t)(D + j + 1) * Kp) = make_float4(w1[0], w1[1], w1[2], w1[3]);
         }
     }
     if (db == 0) *reinterpret_cast<float4 *>(dst + (size_t)(2 * D) * Kp) = make_float4(S0[0], S0[1], S0[2], S0[3]);
