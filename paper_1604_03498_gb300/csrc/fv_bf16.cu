@@ -36,10 +36,10 @@
 // swizzle (TMA writes it; read K-major by the first GEMM and MN-major by the
 // second); gamma^T in 64-component blocks with the 128-byte swizzle.
 //
-// Warp roles (12 warps): 0 TMA producer, 1 MMA issuer, 4-7 and 8-11 two
-// softmax groups taking alternate tiles; warps 2-3 and the tile's softmax
-// group build the tile's Y planes (x copied from the TMA landing buffer,
-// x^2 split, ones).
+// Warp roles (16 warps): 0 TMA producer, 1 MMA issuer, 2-3 and 12-15 build
+// each tile's Y planes (x copied from the TMA landing buffer, x^2 split,
+// ones) while the softmax of the previous tile runs, 4-11 softmax (two warps
+// per TMEM lane quadrant, one per 64-component half, on every tile).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -58,7 +58,7 @@ using namespace sm100;
 
 namespace {
 
-constexpr int kThreads = 384;          // 12 warps
+constexpr int kThreads = 512;          // 16 warps
 constexpr int kRows = 128;             // row tile: M of the first GEMM, K of the second
 constexpr int kComps = 128;            // components per CTA: N of the first GEMM, M of the second
 constexpr uint32_t kBlk = kRows * 32u;           // one [128][16] bf16 block with 32-byte rows (4 KB)
@@ -99,7 +99,6 @@ struct EncArgs {
     int Kp;
     int S;          // CTAs per cluster (Kp / 128), each owning 128 components
     int nstage;     // Y-plane stages (1 or 2)
-    int nslot;      // cluster exchange slots (4, or 2 with a release handshake)
     int ny;         // 3*D16 + 16 columns of Y
     int P;          // 3*D16 + 1 floats per component in a slot
     const float *cl2;         // [Kp] log-constant times log2(e) (-inf on padding)
@@ -111,10 +110,10 @@ struct EncArgs {
 
 struct EncSmem {
     // byte offsets from the (1024-aligned) dynamic shared-memory base
-    uint32_t b, xr, y, y_stage, g, xchg, cl, bars, misc, total;
+    uint32_t b, xr, y, y_stage, g, hx, xchg, cl, bars, misc, total;
 };
 
-__host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage, int nslot) {
+__host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage) {
     EncSmem s;
     uint32_t off = 0;
     s.b = off;                                   // [Qh | Ql | Rh | Rl] x nkb blocks of 128 components
@@ -126,12 +125,14 @@ __host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage, int nslo
     off += nstage * s.y_stage;
     s.g = off;                                   // gamma^T: two 64-component halves
     off += 2u * kGHalf;
-    s.xchg = off;                                // (max, sum) per row: nslot slots x S ranks
-    off += S > 1 ? (uint32_t)nslot * S * kRows * 8u : 0u;
+    s.hx = off;                                  // (max, sum) per row of each column half
+    off += 2u * kRows * 8u;
+    s.xchg = off;                                // (max, sum) per row: 2 slots x S ranks
+    off += S > 1 ? 2u * S * kRows * 8u : 0u;
     s.cl = off;                                  // the CTA's 128 log-constants
     off += kComps * 4u;
     s.bars = off;
-    off += 24u * 8u;
+    off += 32u * 8u;
     s.misc = off;
     off += 16u;
     s.total = off;
@@ -139,9 +140,9 @@ __host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage, int nslo
 }
 
 // Barrier indices. A parity wait cannot tell phase n from phase n + 2, so no
-// thread may skip a phase of a barrier it waits on: barriers that complete
-// once per tile but are waited on by one softmax group (which takes every
-// other tile) come in pairs indexed by the tile's parity.
+// thread may skip a phase of a barrier it waits on; every waiter below waits
+// on every phase (barriers that complete per tile come in pairs indexed by
+// the tile's parity where that keeps two tiles' waits apart).
 enum {
     EB_BFULL = 0,     // GMM operand loaded
     EB_XRFULL = 1,    // [2] x landing buffer loaded (by tile parity)
@@ -152,11 +153,13 @@ enum {
     EB_LEMPTY = 10,   // [2] softmax done with a TMEM buffer
     EB_GFULL = 12,    // gamma^T tile written
     EB_GFREE = 13,    // statistics GEMM done with gamma^T
-    EB_SDONE = 14,    // [2] a unit's statistics complete in TMEM (by the parity of its last tile)
-    EB_TEMPTY = 16,   // statistics accumulator written out
-    EB_DRAIN = 17,
-    EB_XCHG = 18,     // [4] peers' (max, sum) of a tile arrived, by bytes (per exchange slot)
-    EB_XFREE = 22     // [2] peers' warps have read this CTA's (max, sum) (two-slot form)
+    EB_SDONE = 14,    // a unit's statistics complete in TMEM
+    EB_TEMPTY = 15,   // statistics accumulator written out
+    EB_DRAIN = 16,
+    EB_XCHG = 17,     // [2] peers' (max, sum) of a tile arrived, by bytes (slot = tile parity)
+    EB_HXFULL = 19,   // [4] both column halves of a quadrant's rows have written (max, sum)
+    EB_HXFREE = 23,   // [4] both halves have read them
+    EB_NBARS = 27
 };
 
 // Y planes of one tile: x copied from the landing buffer, x^2 split into hi
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, EncArgs p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const EncSmem L = enc_smem(p.nkb, p.S, p.nstage, p.nslot);
+    const EncSmem L = enc_smem(p.nkb, p.S, p.nstage);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);   // [0] tmem base, [1] abort
     volatile uint32_t *abort_flag = misc + 1;
@@ -246,23 +249,23 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[EB_BFULL], 1);
-        mbar_init(&bars[EB_XRFREE], 6);
+        mbar_init(&bars[EB_XRFREE], 6);   // the builder warps
         for (int s = 0; s < 2; ++s) {
             mbar_init(&bars[EB_XRFULL + s], 1);
             mbar_init(&bars[EB_AFULL + s], 6);
             mbar_init(&bars[EB_STFREE + s], 1);
             mbar_init(&bars[EB_LFULL + s], 1);
-            mbar_init(&bars[EB_LEMPTY + s], 4);
-            mbar_init(&bars[EB_SDONE + s], 1);
+            mbar_init(&bars[EB_LEMPTY + s], 8);
+            mbar_init(&bars[EB_XCHG + s], 1);
         }
-        mbar_init(&bars[EB_GFULL], 4);
+        mbar_init(&bars[EB_GFULL], 8);
         mbar_init(&bars[EB_GFREE], 1);
-        mbar_init(&bars[EB_TEMPTY], 4);
+        mbar_init(&bars[EB_SDONE], 1);
+        mbar_init(&bars[EB_TEMPTY], 8);
         mbar_init(&bars[EB_DRAIN], 1);
-        if (p.S > 1) {
-            for (int j = 0; j < p.nslot; ++j) mbar_init(&bars[EB_XCHG + j], 1);
-            if (p.nslot == 2)
-                for (int j = 0; j < 2; ++j) mbar_init(&bars[EB_XFREE + j], (uint32_t)(p.S - 1) * 4);
+        for (int q = 0; q < 4; ++q) {
+            mbar_init(&bars[EB_HXFULL + q], 64);
+            mbar_init(&bars[EB_HXFREE + q], 64);
         }
         misc[1] = 0u;
         fence_mbar_init();
@@ -305,84 +308,96 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         mbar_drain(&bars[EB_BFULL], 0, 200000000ll);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        // Order: L(i), then the statistics GEMM of tile i - lag, where lag is
-        // one with two stages (the next tile's log-likelihoods run while this
-        // tile's softmax works) and zero with one stage.
+        // Issues each tile's log-likelihood GEMM L(i) once its Y planes are
+        // built and its TMEM buffer is free, and each statistics GEMM S(i) once
+        // gamma^T(i) is written (S before L when both are ready: S frees the
+        // stage the builders wait for). Both follow tile order; the barriers
+        // are polled without blocking, under one time bound.
         const uint32_t idesc_l = idesc_bf16(kRows, kComps, false, false);
         const uint32_t idesc_s = idesc_bf16(kComps, p.ny, true, true);
         const uint32_t sB = smem_u32(smem + L.b), sG = smem_u32(smem + L.g);
-        const int lag = p.nstage - 1;
-        struct Pend {
-            int i, s, ui;
-            bool first, last;
-        } prev = {-1, 0, 0, false, false};
-        auto stats = [&](const Pend &t) -> bool {
-            if (t.first && t.ui > 0) {   // the previous unit's accumulator has been written out
-                if (!mbar_wait(&bars[EB_TEMPTY], (t.ui - 1) & 1, abort_flag, p.err)) return false;
-            }
-            if (!mbar_wait(&bars[EB_GFULL], t.i & 1, abort_flag, p.err)) return false;
-            tc_fence_after();
-            const uint32_t sy = smem_u32(smem + L.y + t.s * L.y_stage);
-            for (int q = 0; q < kRows / 16; ++q) {
-                // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
-                // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
-                // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
-                const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
-                const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
-                mma_bf16(tmem + kStatCol, a, b, idesc_s, (t.first && q == 0) ? 0u : 1u);
-            }
-            mma_commit(&bars[EB_GFREE]);
-            mma_commit(&bars[EB_STFREE + (t.i & 1)]);
-            if (t.last) mma_commit(&bars[EB_SDONE + (t.i & 1)]);
-            return true;
-        };
         bool ok = mbar_wait(&bars[EB_BFULL], 0, abort_flag, p.err);
         bool issued = false;
-        int i = 0;
-        for (TileWalk w(p.units, cu); ok && w.more(); w.next(), ++i) {
-            const int s = i % p.nstage, b = i & 1;
-            if (!mbar_wait(&bars[EB_AFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
-            if (i >= 2 && !mbar_wait(&bars[EB_LEMPTY + b], ((i >> 1) - 1) & 1, abort_flag, p.err)) break;
-            tc_fence_after();
-            const uint32_t sA = smem_u32(smem + L.y + s * L.y_stage);
-            const uint32_t d = tmem + (uint32_t)(b * kComps);
-            for (int j = 0; j < p.nkb; ++j) {
-                const uint64_t ax = sdesc_sw32(sA + j * kBlk, 16, 256);
-                const uint64_t ah = sdesc_sw32(sA + plane + j * kBlk, 16, 256);
-                const uint64_t al = sdesc_sw32(sA + 2 * plane + j * kBlk, 16, 256);
-                const uint64_t bqh = sdesc_sw32(sB + (0 * p.nkb + j) * kBlk, 16, 256);
-                const uint64_t bql = sdesc_sw32(sB + (1 * p.nkb + j) * kBlk, 16, 256);
-                const uint64_t brh = sdesc_sw32(sB + (2 * p.nkb + j) * kBlk, 16, 256);
-                const uint64_t brl = sdesc_sw32(sB + (3 * p.nkb + j) * kBlk, 16, 256);
-                mma_bf16(d, ax, bqh, idesc_l, j > 0 ? 1u : 0u);
-                mma_bf16(d, ax, bql, idesc_l, 1u);
-                mma_bf16(d, ah, brh, idesc_l, 1u);
-                mma_bf16(d, ah, brl, idesc_l, 1u);
-                mma_bf16(d, al, brh, idesc_l, 1u);
+        TileWalk wl(p.units, cu), ws(p.units, cu);
+        int nl = 0, ns = 0;   // next tile for L and for S
+        long long t0 = clock64();
+        while (ok && ws.more()) {
+            bool progress = false;
+            if (ns < nl) {
+                bool ready = mbar_test(&bars[EB_GFULL], ns & 1);
+                if (ready && ws.first() && ws.ui > 0)   // the previous unit's accumulator has been written out
+                    ready = mbar_test(&bars[EB_TEMPTY], (ws.ui - 1) & 1);
+                if (ready) {
+                    tc_fence_after();
+                    const uint32_t sy = smem_u32(smem + L.y + (ns % p.nstage) * L.y_stage);
+                    for (int q = 0; q < kRows / 16; ++q) {
+                        // gamma^T: MN-major, 128-byte swizzle, 64-component halves
+                        // kGHalf apart, 8-row groups 1 KB apart; Y: MN-major,
+                        // 16-column blocks kBlk apart, 8-row groups 256 B apart;
+                        // 16 rows per K step
+                        const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
+                        const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                        mma_bf16(tmem + kStatCol, a, b, idesc_s, (ws.first() && q == 0) ? 0u : 1u);
+                    }
+                    mma_commit(&bars[EB_GFREE]);
+                    mma_commit(&bars[EB_STFREE + (ns & 1)]);
+                    if (ws.last()) mma_commit(&bars[EB_SDONE]);
+                    ws.next();
+                    ++ns;
+                    progress = true;
+                }
             }
-            mma_commit(&bars[EB_LFULL + b]);
-            issued = true;
-            const Pend cur = {i, s, w.ui, w.first(), w.last()};
-            if (lag == 0) {
-                ok = stats(cur);
-            } else {
-                if (prev.i >= 0) ok = stats(prev);
-                prev = cur;
+            if (wl.more()) {
+                const int s = nl % p.nstage, b = nl & 1;
+                if (mbar_test(&bars[EB_AFULL + s], (nl / p.nstage) & 1) &&
+                    (nl < 2 || mbar_test(&bars[EB_LEMPTY + b], ((nl >> 1) - 1) & 1))) {
+                    tc_fence_after();
+                    const uint32_t sA = smem_u32(smem + L.y + s * L.y_stage);
+                    const uint32_t d = tmem + (uint32_t)(b * kComps);
+                    for (int j = 0; j < p.nkb; ++j) {
+                        const uint64_t ax = sdesc_sw32(sA + j * kBlk, 16, 256);
+                        const uint64_t ah = sdesc_sw32(sA + plane + j * kBlk, 16, 256);
+                        const uint64_t al = sdesc_sw32(sA + 2 * plane + j * kBlk, 16, 256);
+                        const uint64_t bqh = sdesc_sw32(sB + (0 * p.nkb + j) * kBlk, 16, 256);
+                        const uint64_t bql = sdesc_sw32(sB + (1 * p.nkb + j) * kBlk, 16, 256);
+                        const uint64_t brh = sdesc_sw32(sB + (2 * p.nkb + j) * kBlk, 16, 256);
+                        const uint64_t brl = sdesc_sw32(sB + (3 * p.nkb + j) * kBlk, 16, 256);
+                        mma_bf16(d, ax, bqh, idesc_l, j > 0 ? 1u : 0u);
+                        mma_bf16(d, ax, bql, idesc_l, 1u);
+                        mma_bf16(d, ah, brh, idesc_l, 1u);
+                        mma_bf16(d, ah, brl, idesc_l, 1u);
+                        mma_bf16(d, al, brh, idesc_l, 1u);
+                    }
+                    mma_commit(&bars[EB_LFULL + b]);
+                    issued = true;
+                    wl.next();
+                    ++nl;
+                    progress = true;
+                }
+            }
+            if (progress) {
+                t0 = clock64();
+            } else if (*abort_flag) {
+                ok = false;
+            } else if (clock64() - t0 > 4000000000ll) {
+                *abort_flag = 1u;
+                atomicOr(p.err, kErrTimeout);
+                ok = false;
             }
         }
-        if (ok && lag > 0 && prev.i >= 0) stats(prev);
         if (issued) {   // every issued MMA has finished before TMEM is released
             mma_commit(&bars[EB_DRAIN]);
             mbar_drain(&bars[EB_DRAIN], 0, 2000000000ll);
         }
-    } else if (warp == 2 || warp == 3) {
-        // ---------------- Y builders (with the softmax group of the tile) ----------------
+    } else if (warp == 2 || warp == 3 || warp >= 12) {
+        // ---------------- Y builders: the tile's Y planes from the landing buffer ----------------
+        const int bt = (warp < 12 ? warp - 2 : warp - 10) * 32 + lane;   // 0..191
         int i = 0;
         for (TileWalk w(p.units, cu); w.more(); w.next(), ++i) {
             const int s = i % p.nstage, j = i - p.nstage;   // tile j used this stage before
             if (!mbar_wait(&bars[EB_XRFULL + (i & 1)], (i >> 1) & 1, abort_flag, p.err)) break;
             if (j >= 0 && !mbar_wait(&bars[EB_STFREE + (j & 1)], (j >> 1) & 1, abort_flag, p.err)) break;
-            build_y(smem + L.y + s * L.y_stage, smem + L.xr, plane, p.nkb, w.valid(), threadIdx.x - 64, 192);
+            build_y(smem + L.y + s * L.y_stage, smem + L.xr, plane, p.nkb, w.valid(), bt, 192);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
@@ -391,62 +406,48 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             }
         }
     } else if (warp >= 4) {
-        // ---------------- softmax groups ----------------
-        // Group grp (warps 4-7 or 8-11) takes the tiles with i % 2 == grp and
-        // TMEM buffer grp; warp 4*(grp+1)+q owns rows 32q..32q+31 (its TMEM lane
-        // quadrant), one row per thread, over the CTA's 128 components in four
-        // 32-column chunks. Pass A forms y = l log2(e) + c log2(e), keeps an
-        // online row max/sum with a reference max per chunk and stores
-        // 2^(y - ref) back into TMEM; the cluster's CTAs combine their (max,
-        // sum); pass B rescales each chunk and writes bf16 gamma^T to shared
-        // memory. The group that finishes a unit's last tile then writes the
-        // unit's statistics from TMEM to its slot.
-        const int grp = (warp - 4) >> 2, q = warp & 3;
+        // ---------------- softmax warps ----------------
+        // Eight warps take every tile: warp 4+q and 8+q own rows 32q..32q+31
+        // (their TMEM lane quadrant), one row per thread, over components
+        // 64h..64h+63 (h = 0 for warps 4-7, 1 for 8-11) in two 32-column
+        // chunks. Pass A forms y = l log2(e) + c log2(e), keeps an online row
+        // max/sum with a reference max per chunk and stores 2^(y - ref) back
+        // into TMEM; the two halves of a row combine their (max, sum) through
+        // shared memory, then the cluster's CTAs combine theirs; pass B
+        // rescales each chunk and writes bf16 gamma^T to shared memory. After
+        // a unit's last tile the eight warps write the unit's statistics from
+        // TMEM to its slot (half the columns each).
+        const int h = (warp - 4) >> 2, q = warp & 3;
         const int r = q * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        const float *cl = reinterpret_cast<const float *>(smem + L.cl);
+        const float *cl = reinterpret_cast<const float *>(smem + L.cl) + h * 64;
         float2 *xbuf = reinterpret_cast<float2 *>(smem + L.xchg);
-        uint8_t *gsm = smem + L.g + r * 128;   // this row in the first 64-component half
+        float2 *hx = reinterpret_cast<float2 *>(smem + L.hx);
+        uint8_t *gsm = smem + L.g + h * kGHalf + r * 128;   // this row of this warp's 64-component half
         const int sw = r & 7;                  // 128-byte swizzle: 16-byte chunk j sits at j ^ (row & 7)
-        int i = 0, nflush = 0;
+        int i = 0;
+        TileWalk w(p.units, cu);
         bool ok = true;
-        for (TileWalk w(p.units, cu); ok && w.more(); w.next(), ++i) {
-            if ((i & 1) != grp) continue;
-            {   // help build this tile's Y planes (the group is idle until its log-likelihoods exist)
-                const int s = i % p.nstage, j = i - p.nstage;   // tile j used this stage before
-                if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_XRFULL + (i & 1)], (i >> 1) & 1, abort_flag, p.err)))
-                    break;
-                if (j >= 0 && !__all_sync(0xffffffffu, mbar_wait(&bars[EB_STFREE + (j & 1)], (j >> 1) & 1,
-                                                                 abort_flag, p.err)))
-                    break;
-                build_y(smem + L.y + s * L.y_stage, smem + L.xr, plane, p.nkb, w.valid(), 64 + q * 32 + lane, 192);
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&bars[EB_XRFREE]);
-                    mbar_arrive(&bars[EB_AFULL + s]);
-                }
-            }
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_LFULL + grp], (i >> 1) & 1, abort_flag, p.err))) break;
+        while (ok && w.more()) {
+            const int b = i & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_LFULL + b], (i >> 1) & 1, abort_flag, p.err))) break;
             tc_fence_after();
-            const uint32_t ta = lane_base + (uint32_t)(grp * kComps);
+            const uint32_t ta = lane_base + (uint32_t)(b * kComps + h * 64);
             float m = -INFINITY, z = 0.f;
-            float mc[4];
+            float mc[2];
             uint32_t ra[32], rb[32];
-            // the next chunk's TMEM load is in flight while this chunk is
-            // processed; this chunk's constants are requested before waiting
+            // the second chunk's TMEM load is in flight while the first is
+            // processed; a chunk's constants are requested before its wait
             tmem_ld32_issue(ta, ra);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                uint32_t(&cur)[32] = (c & 1) ? rb : ra;
-                uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
+            for (int c = 0; c < 2; ++c) {
+                uint32_t(&cur)[32] = c ? rb : ra;
                 float4 ccur[8];
 #pragma unroll
                 for (int k4 = 0; k4 < 8; ++k4) ccur[k4] = reinterpret_cast<const float4 *>(cl + c * 32)[k4];
                 tmem_ld_wait(cur);
-                if (c < 3) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
-                // y overwrites l in place (register pressure); four independent
-                // max chains
+                if (c == 0) tmem_ld32_issue(ta + 32, rb);
+                // y overwrites l in place; four independent max chains
                 float cm0 = -INFINITY, cm1 = -INFINITY, cm2 = -INFINITY, cm3 = -INFINITY;
 #pragma unroll
                 for (int k4 = 0; k4 < 8; ++k4) {
@@ -487,105 +488,112 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                 m = mn;
             }
             tmem_st_wait();   // the exponentials are in TMEM before pass B reads them back
+            // the row's two halves: (max, sum) of both, combined in half order
+            // (bounded handshakes: the partner has read the previous tile's
+            // value before this one is written, and written this tile's before
+            // it is read)
+            if (i > 0 && !__all_sync(0xffffffffu, mbar_wait(&bars[EB_HXFREE + q], (i - 1) & 1, abort_flag, p.err)))
+                break;
+            hx[h * kRows + r] = make_float2(m, z);
+            mbar_arrive(&bars[EB_HXFULL + q]);
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_HXFULL + q], i & 1, abort_flag, p.err))) break;
+            const float2 h0 = hx[r], h1 = hx[kRows + r];
+            mbar_arrive(&bars[EB_HXFREE + q]);
+            float mh, zh;
+            {
+                mh = fmaxf(h0.x, h1.x);
+                const float ref = (mh == -INFINITY) ? 0.f : mh;
+                zh = h0.y * ex2_approx(h0.x - ref) + h1.y * ex2_approx(h1.x - ref);
+            }
             // (max, sum) over the cluster, combined in rank order so that every
-            // CTA normalises with the same value. Exchange slot j = i % nslot
-            // of every CTA receives the peers' values for tile i by st.async
-            // (counted in bytes on XCHG[j], which this CTA arms once per use).
-            // With four slots a peer writes slot j again only for tile i + 4,
-            // after this group's contribution to tile i + 2, which follows this
-            // read; with two slots every warp releases the slot (XFREE).
+            // CTA normalises with the same value. Exchange slot i % 2 of every
+            // CTA receives the peers' values for tile i by st.async (counted in
+            // bytes on XCHG, armed once per tile); warps 4-7 send. A peer
+            // writes slot i % 2 again only for tile i + 2, after this CTA's
+            // contribution to tile i + 1, which warps 4-7 send only after the
+            // half handshake of tile i + 1, i.e. after warps 8-11 have read
+            // tile i's values.
             float M = -INFINITY, Z = 0.f;
             if (p.S > 1) {
-                const int j = i % p.nslot;
+                const int j = i & 1;
                 float2 *xb = xbuf + j * p.S * kRows;
-                if (q == 0 && lane == 0)
-                    mbar_arrive_expect_tx(&bars[EB_XCHG + j], (uint32_t)(p.S - 1) * kRows * 8u);
-                if (p.nslot == 2 && i >= 2 &&
-                    !__all_sync(0xffffffffu,
-                                mbar_wait(&bars[EB_XFREE + grp], ((i >> 1) - 1) & 1, abort_flag, p.err, true)))
-                    break;
-                for (int pr = 0; pr < p.S; ++pr) {
-                    if (pr == (int)rank) continue;
-                    st_async_f32x2(mapa(smem_u32(&xb[rank * kRows + r]), (uint32_t)pr), m, z,
-                                   mapa(smem_u32(&bars[EB_XCHG + j]), (uint32_t)pr));
+                if (h == 0) {
+                    if (q == 0 && lane == 0)
+                        mbar_arrive_expect_tx(&bars[EB_XCHG + j], (uint32_t)(p.S - 1) * kRows * 8u);
+                    for (int pr = 0; pr < p.S; ++pr) {
+                        if (pr == (int)rank) continue;
+                        st_async_f32x2(mapa(smem_u32(&xb[rank * kRows + r]), (uint32_t)pr), mh, zh,
+                                       mapa(smem_u32(&bars[EB_XCHG + j]), (uint32_t)pr));
+                    }
                 }
                 if (!__all_sync(0xffffffffu,
-                                mbar_wait(&bars[EB_XCHG + j], (i / p.nslot) & 1, abort_flag, p.err, true)))
+                                mbar_wait(&bars[EB_XCHG + j], (i >> 1) & 1, abort_flag, p.err, true)))
                     break;
                 for (int pr = 0; pr < p.S; ++pr) {
-                    const float2 v = pr == (int)rank ? make_float2(m, z) : xb[pr * kRows + r];
+                    const float2 v = pr == (int)rank ? make_float2(mh, zh) : xb[pr * kRows + r];
                     const float Mn = fmaxf(M, v.x);
                     const float ref = (Mn == -INFINITY) ? 0.f : Mn;
                     Z = Z * ex2_approx(M - ref) + v.y * ex2_approx(v.x - ref);
                     M = Mn;
                 }
-                if (p.nslot == 2) {
-                    __syncwarp();   // the warp's reads are done before its release
-                    if (lane == 0)
-                        for (int pr = 0; pr < p.S; ++pr)
-                            if (pr != (int)rank)
-                                mbar_arrive_remote(mapa(smem_u32(&bars[EB_XFREE + grp]), (uint32_t)pr));
-                }
             } else {
-                M = m;
-                Z = z;
+                M = mh;
+                Z = zh;
             }
             const float Mref = (M == -INFINITY) ? 0.f : M;
             const float inv = 1.0f / Z;
             // the statistics GEMM of the previous tile has read gamma^T. No
             // phase can be skipped here: L(i) was issued after the statistics
             // GEMM of tile i - 2, so that phase completed before LFULL(i).
-            if (i >= 1 && !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], (i - 1) & 1, abort_flag, p.err))) break;
-            // pass B: normalised posteriors -> bf16 gamma^T (next chunk's load in flight)
+            if (i >= 1 &&
+                !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], (i - 1) & 1, abort_flag, p.err))) break;
+            // pass B: normalised posteriors -> bf16 gamma^T (second chunk's load in flight)
             tmem_ld32_issue(ta, ra);
             tmem_ld_wait(ra);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                uint32_t(&cur)[32] = (c & 1) ? rb : ra;
-                uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
-                if (c < 3) tmem_ld32_issue(ta + (c + 1) * 32, nxt);
+            for (int c = 0; c < 2; ++c) {
+                uint32_t(&cur)[32] = c ? rb : ra;
+                if (c == 0) tmem_ld32_issue(ta + 32, rb);
                 const float sc = ex2_approx(mc[c] - Mref) * inv;
-                uint8_t *gh = gsm + (c >> 1) * kGHalf;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {   // 16-byte chunk (c & 1) * 4 + k of the 128-byte row
+                for (int k = 0; k < 4; ++k) {   // 16-byte chunk c * 4 + k of the 128-byte row
                     uint4 v;
                     v.x = pack_bf16x2(__uint_as_float(cur[8 * k + 0]) * sc, __uint_as_float(cur[8 * k + 1]) * sc);
                     v.y = pack_bf16x2(__uint_as_float(cur[8 * k + 2]) * sc, __uint_as_float(cur[8 * k + 3]) * sc);
                     v.z = pack_bf16x2(__uint_as_float(cur[8 * k + 4]) * sc, __uint_as_float(cur[8 * k + 5]) * sc);
                     v.w = pack_bf16x2(__uint_as_float(cur[8 * k + 6]) * sc, __uint_as_float(cur[8 * k + 7]) * sc);
-                    *reinterpret_cast<uint4 *>(gh + ((((c & 1) * 4 + k) ^ sw) << 4)) = v;
+                    *reinterpret_cast<uint4 *>(gsm + (((c * 4 + k) ^ sw) << 4)) = v;
                 }
-                if (c < 3) tmem_ld_wait(nxt);
+                if (c == 0) tmem_ld_wait(rb);
             }
             fence_proxy_async_smem();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&bars[EB_GFULL]);
-                mbar_arrive(&bars[EB_LEMPTY + grp]);
+                mbar_arrive(&bars[EB_LEMPTY + b]);
             }
-            if (!w.last()) continue;
+            const bool last = w.last();
+            const int uidx = w.ui, uslot = w.slot();
+            w.next();
+            ++i;
+            if (!last) continue;
             // the unit's statistics: TMEM -> slot part[slot][j][Kp]. Slot
             // columns follow the TMEM columns ([S1 | S2hi | S2lo] blocks of
-            // D16, then S0, the first ones column), so this is a copy; two
-            // 32-column loads are in flight at a time.
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_SDONE + grp], nflush & 1, abort_flag, p.err))) break;
-            ++nflush;
+            // D16, then S0, the first ones column), so this is a copy; warps
+            // 4-7 take 32-column groups 0, 2, ..., warps 8-11 groups 1, 3, ...
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_SDONE], uidx & 1, abort_flag, p.err))) break;
             tc_fence_after();
             const int k = (int)rank * kComps + r;
-            float *dst = p.part + (size_t)w.slot() * p.Kp * p.P + k;
+            float *dst = p.part + (size_t)uslot * p.Kp * p.P + k;
             const uint32_t ts = lane_base + kStatCol;
-            for (int n0 = 0; n0 < p.P; n0 += 64) {
-                uint32_t va[32], vb[32];
+            for (int n0 = h * 32; n0 < p.P; n0 += 64) {
+                uint32_t va[32];
                 tmem_ld32_issue(ts + n0, va);
-                tmem_ld32_issue(ts + n0 + 32, vb);
                 tmem_ld_wait(va);
-                tmem_ld_wait(vb);
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
+                for (int e = 0; e < 32; ++e)
                     if (n0 + e < p.P) dst[(size_t)(n0 + e) * p.Kp] = __uint_as_float(va[e]);
-                    if (n0 + 32 + e < p.P) dst[(size_t)(n0 + 32 + e) * p.Kp] = __uint_as_float(vb[e]);
-                }
             }
             tc_fence_before();
             __syncwarp();
@@ -643,7 +651,7 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, ui
 }
 
 struct EncCfg {
-    int nkb, S, nstage, nslot, ny;
+    int nkb, S, nstage, ny;
     size_t smem;
 };
 
@@ -651,18 +659,8 @@ bool enc_config(const fv_gmm *g, EncCfg &c) {
     c.nkb = round_up(g->D, 16) / 16;
     c.S = g->Kp / kComps;
     c.ny = 3 * c.nkb * 16 + 16;
-    // prefer two Y stages, then four exchange slots
-    c.nstage = 1;
-    c.nslot = 2;
-    if (enc_smem(c.nkb, c.S, 2, 4).total <= (uint32_t)kMaxSmem) {
-        c.nstage = 2;
-        c.nslot = 4;
-    } else if (enc_smem(c.nkb, c.S, 2, 2).total <= (uint32_t)kMaxSmem) {
-        c.nstage = 2;
-    } else if (enc_smem(c.nkb, c.S, 1, 4).total <= (uint32_t)kMaxSmem) {
-        c.nslot = 4;
-    }
-    c.smem = enc_smem(c.nkb, c.S, c.nstage, c.nslot).total;
+    c.nstage = enc_smem(c.nkb, c.S, 2).total <= (uint32_t)kMaxSmem ? 2 : 1;
+    c.smem = enc_smem(c.nkb, c.S, c.nstage).total;
     return g->Kp % kComps == 0 && c.S >= 1 && c.S <= 4 && c.ny <= 256 && c.smem <= (size_t)kMaxSmem;
 }
 
@@ -748,7 +746,6 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     a.Kp = g->Kp;
     a.S = c.S;
     a.nstage = c.nstage;
-    a.nslot = c.nslot;
     a.ny = c.ny;
     a.P = P;
     a.cl2 = g->dev.cl2;
