@@ -146,7 +146,7 @@ __host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage) {
 enum {
     EB_BFULL = 0,     // GMM operand loaded
     EB_XRFULL = 1,    // [2] x landing buffer loaded (by tile parity)
-    EB_XRFREE = 3,    // x landing buffer copied out
+    EB_DRAIN2 = 3,    // the statistics issuer's MMAs done
     EB_AFULL = 4,     // [2] Y planes of a stage built
     EB_STFREE = 6,    // [2] both GEMMs done with a tile's stage (by tile parity)
     EB_LFULL = 8,     // [2] log-likelihoods of a TMEM buffer ready
@@ -249,7 +249,7 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[EB_BFULL], 1);
-        mbar_init(&bars[EB_XRFREE], 6);   // the builder warps
+        mbar_init(&bars[EB_DRAIN2], 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(&bars[EB_XRFULL + s], 1);
             mbar_init(&bars[EB_AFULL + s], 6);
@@ -284,7 +284,11 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
     const uint32_t plane = (uint32_t)p.nkb * kBlk;   // one of the X, X2hi, X2lo planes
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
+        // ---------------- TMA loads and log-likelihood GEMMs ----------------
+        // Tile i's Y planes built (AFULL) also frees the landing buffer, so
+        // x of tile i + 1 is requested then; L(i) follows once its TMEM
+        // buffer is free. (Issuing L blocks this thread for most of its
+        // duration, so the statistics GEMMs have their own thread.)
         prefetch_tmap(&tmX);
         prefetch_tmap(&tmB);
         mbar_arrive_expect_tx(&bars[EB_BFULL], 4u * plane);
@@ -292,102 +296,86 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             for (int j = 0; j < p.nkb; ++j)
                 tma_load_2d(smem + L.b + (t * p.nkb + j) * kBlk, &tmB, &bars[EB_BFULL], j * 16,
                             t * p.Kp + (int)rank * kComps);
-        // x of tile i lands in the landing buffer as soon as tile i - 1 has
-        // been copied out of it, well before tile i's stage is free
-        int last = -1;
-        int i = 0;
-        for (TileWalk w(p.units, cu); w.more(); w.next(), ++i) {
-            if (i > 0 && !mbar_wait(&bars[EB_XRFREE], (i - 1) & 1, abort_flag, p.err)) break;
+        const uint32_t idesc_l = idesc_bf16(kRows, kComps, false, false);
+        const uint32_t sB = smem_u32(smem + L.b);
+        TileWalk w(p.units, cu), wn(p.units, cu);
+        int last_load = -1;
+        auto load_x = [&](int i, int row0) {
             mbar_arrive_expect_tx(&bars[EB_XRFULL + (i & 1)], plane);
             for (int j = 0; j < p.nkb; ++j)
-                tma_load_2d(smem + L.xr + j * kBlk, &tmX, &bars[EB_XRFULL + (i & 1)], j * 16, w.row0());
-            last = i;
+                tma_load_2d(smem + L.xr + j * kBlk, &tmX, &bars[EB_XRFULL + (i & 1)], j * 16, row0);
+            last_load = i;
+        };
+        if (wn.more()) {
+            load_x(0, wn.row0());
+            wn.next();
         }
-        // wait (bounded, even when aborting) for this thread's copies still in flight
-        if (last >= 0) mbar_drain(&bars[EB_XRFULL + (last & 1)], (last >> 1) & 1, 200000000ll);
-        mbar_drain(&bars[EB_BFULL], 0, 200000000ll);
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        // Issues each tile's log-likelihood GEMM L(i) once its Y planes are
-        // built and its TMEM buffer is free, and each statistics GEMM S(i) once
-        // gamma^T(i) is written (S before L when both are ready: S frees the
-        // stage the builders wait for). Both follow tile order; the barriers
-        // are polled without blocking, under one time bound.
-        const uint32_t idesc_l = idesc_bf16(kRows, kComps, false, false);
-        const uint32_t idesc_s = idesc_bf16(kComps, p.ny, true, true);
-        const uint32_t sB = smem_u32(smem + L.b), sG = smem_u32(smem + L.g);
         bool ok = mbar_wait(&bars[EB_BFULL], 0, abort_flag, p.err);
         bool issued = false;
-        TileWalk wl(p.units, cu), ws(p.units, cu);
-        int nl = 0, ns = 0;   // next tile for L and for S
-        long long t0 = clock64();
-        while (ok && ws.more()) {
-            bool progress = false;
-            if (ns < nl) {
-                bool ready = mbar_test(&bars[EB_GFULL], ns & 1);
-                if (ready && ws.first() && ws.ui > 0)   // the previous unit's accumulator has been written out
-                    ready = mbar_test(&bars[EB_TEMPTY], (ws.ui - 1) & 1);
-                if (ready) {
-                    tc_fence_after();
-                    const uint32_t sy = smem_u32(smem + L.y + (ns % p.nstage) * L.y_stage);
-                    for (int q = 0; q < kRows / 16; ++q) {
-                        // gamma^T: MN-major, 128-byte swizzle, 64-component halves
-                        // kGHalf apart, 8-row groups 1 KB apart; Y: MN-major,
-                        // 16-column blocks kBlk apart, 8-row groups 256 B apart;
-                        // 16 rows per K step
-                        const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
-                        const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
-                        mma_bf16(tmem + kStatCol, a, b, idesc_s, (ws.first() && q == 0) ? 0u : 1u);
-                    }
-                    mma_commit(&bars[EB_GFREE]);
-                    mma_commit(&bars[EB_STFREE + (ns & 1)]);
-                    if (ws.last()) mma_commit(&bars[EB_SDONE]);
-                    ws.next();
-                    ++ns;
-                    progress = true;
-                }
+        for (int i = 0; ok && w.more(); w.next(), ++i) {
+            const int s = i % p.nstage, b = i & 1;
+            if (!mbar_wait(&bars[EB_AFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
+            if (wn.more()) {
+                load_x(i + 1, wn.row0());
+                wn.next();
             }
-            if (wl.more()) {
-                const int s = nl % p.nstage, b = nl & 1;
-                if (mbar_test(&bars[EB_AFULL + s], (nl / p.nstage) & 1) &&
-                    (nl < 2 || mbar_test(&bars[EB_LEMPTY + b], ((nl >> 1) - 1) & 1))) {
-                    tc_fence_after();
-                    const uint32_t sA = smem_u32(smem + L.y + s * L.y_stage);
-                    const uint32_t d = tmem + (uint32_t)(b * kComps);
-                    for (int j = 0; j < p.nkb; ++j) {
-                        const uint64_t ax = sdesc_sw32(sA + j * kBlk, 16, 256);
-                        const uint64_t ah = sdesc_sw32(sA + plane + j * kBlk, 16, 256);
-                        const uint64_t al = sdesc_sw32(sA + 2 * plane + j * kBlk, 16, 256);
-                        const uint64_t bqh = sdesc_sw32(sB + (0 * p.nkb + j) * kBlk, 16, 256);
-                        const uint64_t bql = sdesc_sw32(sB + (1 * p.nkb + j) * kBlk, 16, 256);
-                        const uint64_t brh = sdesc_sw32(sB + (2 * p.nkb + j) * kBlk, 16, 256);
-                        const uint64_t brl = sdesc_sw32(sB + (3 * p.nkb + j) * kBlk, 16, 256);
-                        mma_bf16(d, ax, bqh, idesc_l, j > 0 ? 1u : 0u);
-                        mma_bf16(d, ax, bql, idesc_l, 1u);
-                        mma_bf16(d, ah, brh, idesc_l, 1u);
-                        mma_bf16(d, ah, brl, idesc_l, 1u);
-                        mma_bf16(d, al, brh, idesc_l, 1u);
-                    }
-                    mma_commit(&bars[EB_LFULL + b]);
-                    issued = true;
-                    wl.next();
-                    ++nl;
-                    progress = true;
-                }
+            if (i >= 2 && !mbar_wait(&bars[EB_LEMPTY + b], ((i >> 1) - 1) & 1, abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + L.y + s * L.y_stage);
+            const uint32_t d = tmem + (uint32_t)(b * kComps);
+            for (int j = 0; j < p.nkb; ++j) {
+                const uint64_t ax = sdesc_sw32(sA + j * kBlk, 16, 256);
+                const uint64_t ah = sdesc_sw32(sA + plane + j * kBlk, 16, 256);
+                const uint64_t al = sdesc_sw32(sA + 2 * plane + j * kBlk, 16, 256);
+                const uint64_t bqh = sdesc_sw32(sB + (0 * p.nkb + j) * kBlk, 16, 256);
+                const uint64_t bql = sdesc_sw32(sB + (1 * p.nkb + j) * kBlk, 16, 256);
+                const uint64_t brh = sdesc_sw32(sB + (2 * p.nkb + j) * kBlk, 16, 256);
+                const uint64_t brl = sdesc_sw32(sB + (3 * p.nkb + j) * kBlk, 16, 256);
+                mma_bf16(d, ax, bqh, idesc_l, j > 0 ? 1u : 0u);
+                mma_bf16(d, ax, bql, idesc_l, 1u);
+                mma_bf16(d, ah, brh, idesc_l, 1u);
+                mma_bf16(d, ah, brl, idesc_l, 1u);
+                mma_bf16(d, al, brh, idesc_l, 1u);
             }
-            if (progress) {
-                t0 = clock64();
-            } else if (*abort_flag) {
-                ok = false;
-            } else if (clock64() - t0 > 4000000000ll) {
-                *abort_flag = 1u;
-                atomicOr(p.err, kErrTimeout);
-                ok = false;
-            }
+            mma_commit(&bars[EB_LFULL + b]);
+            issued = true;
         }
         if (issued) {   // every issued MMA has finished before TMEM is released
             mma_commit(&bars[EB_DRAIN]);
             mbar_drain(&bars[EB_DRAIN], 0, 2000000000ll);
+        }
+        // wait (bounded, even when aborting) for this thread's copies still in flight
+        if (last_load >= 0) mbar_drain(&bars[EB_XRFULL + (last_load & 1)], (last_load >> 1) & 1, 200000000ll);
+        mbar_drain(&bars[EB_BFULL], 0, 200000000ll);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- statistics GEMMs ----------------
+        const uint32_t idesc_s = idesc_bf16(kComps, p.ny, true, true);
+        const uint32_t sG = smem_u32(smem + L.g);
+        bool issued = false;
+        int i = 0;
+        for (TileWalk w(p.units, cu); w.more(); w.next(), ++i) {
+            if (w.first() && w.ui > 0) {   // the previous unit's accumulator has been written out
+                if (!mbar_wait(&bars[EB_TEMPTY], (w.ui - 1) & 1, abort_flag, p.err)) break;
+            }
+            if (!mbar_wait(&bars[EB_GFULL], i & 1, abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint32_t sy = smem_u32(smem + L.y + (i % p.nstage) * L.y_stage);
+            for (int q = 0; q < kRows / 16; ++q) {
+                // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
+                // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
+                // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
+                const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
+                const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                mma_bf16(tmem + kStatCol, a, b, idesc_s, (w.first() && q == 0) ? 0u : 1u);
+            }
+            mma_commit(&bars[EB_GFREE]);
+            mma_commit(&bars[EB_STFREE + (i & 1)]);
+            if (w.last()) mma_commit(&bars[EB_SDONE]);
+            issued = true;
+        }
+        if (issued) {
+            mma_commit(&bars[EB_DRAIN2]);
+            mbar_drain(&bars[EB_DRAIN2], 0, 2000000000ll);
         }
     } else if (warp == 2 || warp == 3 || warp >= 12) {
         // ---------------- Y builders: the tile's Y planes from the landing buffer ----------------
@@ -398,12 +386,9 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             if (!mbar_wait(&bars[EB_XRFULL + (i & 1)], (i >> 1) & 1, abort_flag, p.err)) break;
             if (j >= 0 && !mbar_wait(&bars[EB_STFREE + (j & 1)], (j >> 1) & 1, abort_flag, p.err)) break;
             build_y(smem + L.y + s * L.y_stage, smem + L.xr, plane, p.nkb, w.valid(), bt, 192);
-            fence_proxy_async_smem();
+            fence_proxy_async_smem();   // also orders the landing-buffer reads before its next TMA write
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&bars[EB_XRFREE]);
-                mbar_arrive(&bars[EB_AFULL + s]);
-            }
+            if (lane == 0) mbar_arrive(&bars[EB_AFULL + s]);
         }
     } else if (warp >= 4) {
         // ---------------- softmax warps ----------------
@@ -542,9 +527,8 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             }
             const float Mref = (M == -INFINITY) ? 0.f : M;
             const float inv = 1.0f / Z;
-            // the statistics GEMM of the previous tile has read gamma^T. No
-            // phase can be skipped here: L(i) was issued after the statistics
-            // GEMM of tile i - 2, so that phase completed before LFULL(i).
+            // the statistics GEMM of the previous tile has read gamma^T (these
+            // warps wait on every phase of GFREE in order, so none is skipped)
             if (i >= 1 &&
                 !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], (i - 1) & 1, abort_flag, p.err))) break;
             // pass B: normalised posteriors -> bf16 gamma^T (second chunk's load in flight)
