@@ -83,16 +83,33 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
 
         for (int d0 = 0; d0 < D; d0 += P_DS) {
             __syncthreads();
-            for (int i = tid; i < P_DS * KC; i += P_THREADS) {
+            // fixed trip counts, unrolled: every load of the stage is in
+            // flight before the first shared-memory store
+            float gs[P_DS * KC / P_THREADS], gn[P_DS * KC / P_THREADS], gx[P_DS * P_BM / P_THREADS];
+#pragma unroll
+            for (int it = 0; it < P_DS * KC / P_THREADS; ++it) {
+                const int i = tid + it * P_THREADS;
                 const int dd = i / KC, kk = i % KC, d = d0 + dd;
                 const bool ok = d < D;
-                sS[i] = ok ? s_t[(size_t)d * Kp + kc0 + kk] : 0.f;
-                sN[i] = ok ? nms_t[(size_t)d * Kp + kc0 + kk] : 0.f;
+                gs[it] = ok ? s_t[(size_t)d * Kp + kc0 + kk] : 0.f;
+                gn[it] = ok ? nms_t[(size_t)d * Kp + kc0 + kk] : 0.f;
             }
-            for (int i = tid; i < P_DS * P_BM; i += P_THREADS) {
+#pragma unroll
+            for (int it = 0; it < P_DS * P_BM / P_THREADS; ++it) {
+                const int i = tid + it * P_THREADS;
                 const int r = i / P_DS, dd = i % P_DS, d = d0 + dd;
                 const int64_t row = row0 + r;
-                sX[dd * XS + r] = (row < rows && d < D) ? X[row * D + d] : 0.f;
+                gx[it] = (row < rows && d < D) ? X[row * D + d] : 0.f;
+            }
+#pragma unroll
+            for (int it = 0; it < P_DS * KC / P_THREADS; ++it) {
+                sS[tid + it * P_THREADS] = gs[it];
+                sN[tid + it * P_THREADS] = gn[it];
+            }
+#pragma unroll
+            for (int it = 0; it < P_DS * P_BM / P_THREADS; ++it) {
+                const int i = tid + it * P_THREADS;
+                sX[(i % P_DS) * XS + i / P_DS] = gx[it];
             }
             __syncthreads();
 #pragma unroll 4
