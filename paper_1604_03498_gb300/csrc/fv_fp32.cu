@@ -192,13 +192,27 @@ constexpr int S_CPT = 4;   // components per thread
 constexpr int S_DPT = 8;   // dimensions per thread
 constexpr int S_THREADS = (S_KC / S_CPT) * (S_DC / S_DPT);  // 128
 
-constexpr int S_PER_THREAD = S_RS * S_KC / S_THREADS;  // 16 staged values of each kind per thread
+constexpr int S_BLOCKS_PER_SM = 3;
+
+// Asynchronous global -> shared copies (cp.async): `bytes` of 4 or 16, zero
+// fill when !valid (the source is then not read; a valid address is passed).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // grid.x = statistics units (row ranges), grid.y = 64-component chunks,
-// grid.z = 64-dimension chunks. Stages of 32 rows are double-buffered: the
-// next stage's posteriors and descriptors are loaded into registers while the
-// current one is consumed from shared memory.
-__global__ void __launch_bounds__(S_THREADS, 3)
+// grid.z = 64-dimension chunks. Stages of 32 rows are double-buffered in
+// shared memory and filled by cp.async (16-byte copies when the rows allow,
+// VEC) while the previous stage is consumed.
+template <bool VEC>
+__global__ void __launch_bounds__(S_THREADS, S_BLOCKS_PER_SM)
 f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ gamma, int Kp, int Dp,
                  const float *__restrict__ mu_kd, const StatUnit *__restrict__ units, float *__restrict__ part,
                  int P) {
@@ -211,6 +225,35 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     const int cg = tid & 15, dg = tid >> 4;
     const int kb = kc0 + cg * S_CPT, dl = dg * S_DPT, db = dc0 + dl;
     const bool active = db < D;
+
+    // stage r0 -> buffer b: gamma[row][kc0..kc0+63] and X[row][dc0..dc0+63]
+    auto issue = [&](int r0, int b) {
+        if constexpr (VEC) {
+#pragma unroll
+            for (int q = 0; q < S_RS * S_KC / 4 / S_THREADS; ++q) {   // 16-byte chunks
+                const int i = tid + q * S_THREADS;
+                const int r = i >> 4, c4 = (i & 15) * 4;
+                const bool rok = r0 + r < u.nrows;
+                const int64_t row = u.row0 + r0 + r;
+                cp_async<16>(&sG[b][r * S_KC + c4], rok ? gamma + row * Kp + kc0 + c4 : gamma, rok);
+                const bool xok = rok && dc0 + c4 < D;
+                cp_async<16>(&sXs[b][r * S_DC + c4], xok ? X + row * D + dc0 + c4 : X, xok);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < S_RS * S_KC / S_THREADS; ++q) {
+                const int i = tid + q * S_THREADS;
+                const int r = i / S_KC, kk = i % S_KC;
+                const bool rok = r0 + r < u.nrows;
+                const int64_t row = u.row0 + r0 + r;
+                cp_async<4>(&sG[b][i], rok ? gamma + row * Kp + kc0 + kk : gamma, rok);
+                const bool xok = rok && dc0 + kk < D;
+                cp_async<4>(&sXs[b][i], xok ? X + row * D + dc0 + kk : X, xok);
+            }
+        }
+        cp_async_commit();
+    };
+    issue(0, 0);
 
     uint64_t nm[S_CPT][S_DPT / 2], U[S_CPT][S_DPT / 2], W[S_CPT][S_DPT / 2];
     float S0[S_CPT];
@@ -227,33 +270,12 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
         }
     }
 
-    float rg[S_PER_THREAD], rx[S_PER_THREAD];
-    auto load = [&](int r0) {
-#pragma unroll
-        for (int q = 0; q < S_PER_THREAD; ++q) {
-            const int i = tid + q * S_THREADS;
-            const int r = i / S_KC, kk = i % S_KC, d = dc0 + kk;
-            const bool rok = r0 + r < u.nrows;
-            const int64_t row = u.row0 + r0 + r;
-            rg[q] = rok ? gamma[row * Kp + kc0 + kk] : 0.f;
-            rx[q] = (rok && d < D) ? X[row * D + d] : 0.f;
-        }
-    };
-    auto store = [&](int b) {
-#pragma unroll
-        for (int q = 0; q < S_PER_THREAD; ++q) {
-            sG[b][tid + q * S_THREADS] = rg[q];
-            sXs[b][tid + q * S_THREADS] = rx[q];
-        }
-    };
-
-    load(0);
-    store(0);
-    __syncthreads();
     int buf = 0;
     for (int r0 = 0; r0 < u.nrows; r0 += S_RS) {
-        const bool more = r0 + S_RS < u.nrows;
-        if (more) load(r0 + S_RS);
+        if (r0 + S_RS < u.nrows) issue(r0 + S_RS, buf ^ 1);
+        else cp_async_commit();   // an empty group keeps the wait count uniform
+        cp_async_wait1();         // this stage's copies (of this thread) have landed
+        __syncthreads();          // ... and every thread's
         if (active) {
             const float *G = sG[buf];
             const float *Xs = sXs[buf];
@@ -278,8 +300,7 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
                 }
             }
         }
-        if (more) store(buf ^ 1);
-        __syncthreads();
+        __syncthreads();   // the buffer is consumed before it is refilled
         buf ^= 1;
     }
     if (!active) return;
@@ -340,9 +361,16 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
                              int n_units, float *part, int P, cudaStream_t st) {
     if (n_units <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_units, (unsigned)(g->Kp / S_KC), (unsigned)((g->D + S_DC - 1) / S_DC));
+    // 16-byte copies need 16-byte aligned rows of X (gamma rows always are)
+    const bool vec = (g->D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     {
         KernelTimer kt_("f32_stats", st);
-        f32_stats_kernel<<<grid, S_THREADS, 0, st>>>(X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units, part, P);
+        if (vec)
+            f32_stats_kernel<true><<<grid, S_THREADS, 0, st>>>(X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units,
+                                                               part, P);
+        else
+            f32_stats_kernel<false><<<grid, S_THREADS, 0, st>>>(X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units,
+                                                                part, P);
     }
     return cudaGetLastError();
 }
