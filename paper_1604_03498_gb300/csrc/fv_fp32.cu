@@ -50,14 +50,30 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     return r;
 }
 
+// Asynchronous global -> shared copies (cp.async): `bytes` of 4 or 16, zero
+// fill when !valid (the source is then not read; a valid address is passed).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 constexpr int P_BM = 64;   // rows per posterior block
-constexpr int P_DS = 32;   // dimension slice staged in shared memory
+constexpr int P_DS = 16;   // dimension slice staged in shared memory
 constexpr int P_THREADS = 256;
 
 // Dynamic shared memory layout of the posteriors kernel:
-//   sS[P_DS][KC], sN[P_DS][KC]   1/sigma and -mu/sigma of the current chunk
-//   sX[P_DS][P_BM + 4]           descriptor slice, dimension-major
-//   sL[P_BM][Kp]                 log-likelihoods of the row block
+//   two stages of
+//     sS[P_DS][KC], sN[P_DS][KC]   1/sigma and -mu/sigma of a (component chunk, dimension slice)
+//     sX[P_DS][P_BM + 4]           descriptor slice, dimension-major
+//   sL[P_BM][Kp]                   log-likelihoods of the row block
+// The (chunk, slice) phases run in order; phase p + 1 is copied in by
+// cp.async while phase p is computed.
 template <int CPL>
 __global__ void __launch_bounds__(P_THREADS)
 f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
@@ -65,101 +81,99 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
                       const float *__restrict__ cst, float *__restrict__ gamma) {
     constexpr int KC = 32 * CPL;
     constexpr int XS = P_BM + 4;
+    constexpr int STAGE = 2 * P_DS * KC + P_DS * XS;
     extern __shared__ __align__(16) float smem[];
-    float *sS = smem;
-    float *sN = sS + P_DS * KC;
-    float *sX = sN + P_DS * KC;
-    float *sL = sX + P_DS * XS;
+    float *sL = smem + 2 * STAGE;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t row0 = (int64_t)blockIdx.x * P_BM;
+    const int nslice = (D + P_DS - 1) / P_DS, nphase = (Kp / KC) * nslice;
 
-    for (int kc0 = 0; kc0 < Kp; kc0 += KC) {
-        uint64_t acc[8][CPL / 2];   // component pairs
+    auto issue = [&](int ph, int b) {
+        const int kc0 = (ph / nslice) * KC, d0 = (ph % nslice) * P_DS;
+        float *bS = smem + b * STAGE, *bN = bS + P_DS * KC, *bX = bN + P_DS * KC;
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int c = 0; c < CPL / 2; ++c) acc[r][c] = 0ull;
-
-        for (int d0 = 0; d0 < D; d0 += P_DS) {
-            __syncthreads();
-            // fixed trip counts, unrolled: every load of the stage is in
-            // flight before the first shared-memory store
-            float gs[P_DS * KC / P_THREADS], gn[P_DS * KC / P_THREADS], gx[P_DS * P_BM / P_THREADS];
-#pragma unroll
-            for (int it = 0; it < P_DS * KC / P_THREADS; ++it) {
-                const int i = tid + it * P_THREADS;
-                const int dd = i / KC, kk = i % KC, d = d0 + dd;
-                const bool ok = d < D;
-                gs[it] = ok ? s_t[(size_t)d * Kp + kc0 + kk] : 0.f;
-                gn[it] = ok ? nms_t[(size_t)d * Kp + kc0 + kk] : 0.f;
-            }
-#pragma unroll
-            for (int it = 0; it < P_DS * P_BM / P_THREADS; ++it) {
-                const int i = tid + it * P_THREADS;
-                const int r = i / P_DS, dd = i % P_DS, d = d0 + dd;
-                const int64_t row = row0 + r;
-                gx[it] = (row < rows && d < D) ? X[row * D + d] : 0.f;
-            }
-#pragma unroll
-            for (int it = 0; it < P_DS * KC / P_THREADS; ++it) {
-                sS[tid + it * P_THREADS] = gs[it];
-                sN[tid + it * P_THREADS] = gn[it];
-            }
-#pragma unroll
-            for (int it = 0; it < P_DS * P_BM / P_THREADS; ++it) {
-                const int i = tid + it * P_THREADS;
-                sX[(i % P_DS) * XS + i / P_DS] = gx[it];
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int dd = 0; dd < P_DS; ++dd) {
-                const float4 xa = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8]);
-                const float4 xb = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8 + 4]);
-                const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-                float sv[CPL], nv[CPL];
-                if constexpr (CPL == 4) {
-                    const float4 a = *reinterpret_cast<const float4 *>(&sS[dd * KC + lane * 4]);
-                    const float4 b = *reinterpret_cast<const float4 *>(&sN[dd * KC + lane * 4]);
-                    sv[0] = a.x; sv[1] = a.y; sv[2] = a.z; sv[3] = a.w;
-                    nv[0] = b.x; nv[1] = b.y; nv[2] = b.z; nv[3] = b.w;
-                } else {
-                    const float2 a = *reinterpret_cast<const float2 *>(&sS[dd * KC + lane * 2]);
-                    const float2 b = *reinterpret_cast<const float2 *>(&sN[dd * KC + lane * 2]);
-                    sv[0] = a.x; sv[1] = a.y;
-                    nv[0] = b.x; nv[1] = b.y;
-                }
-                uint64_t s2[CPL / 2], n2[CPL / 2];
-#pragma unroll
-                for (int c = 0; c < CPL / 2; ++c) {
-                    s2[c] = pk2(sv[2 * c], sv[2 * c + 1]);
-                    n2[c] = pk2(nv[2 * c], nv[2 * c + 1]);
-                }
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const uint64_t x2 = pk2(xv[r], xv[r]);
-#pragma unroll
-                    for (int c = 0; c < CPL / 2; ++c) {
-                        const uint64_t t = fma2(x2, s2[c], n2[c]);
-                        acc[r][c] = fma2(t, t, acc[r][c]);
-                    }
-                }
-            }
+        for (int q = 0; q < P_DS * KC / 4 / P_THREADS; ++q) {   // 16-byte chunks of the GMM slices
+            const int i = tid + q * P_THREADS;
+            const int dd = i / (KC / 4), c4 = (i % (KC / 4)) * 4, d = d0 + dd;
+            const bool ok = d < D;
+            cp_async<16>(bS + dd * KC + c4, ok ? s_t + (size_t)d * Kp + kc0 + c4 : s_t, ok);
+            cp_async<16>(bN + dd * KC + c4, ok ? nms_t + (size_t)d * Kp + kc0 + c4 : nms_t, ok);
         }
-        // l = c' - dist/2 for this chunk
 #pragma unroll
-        for (int c = 0; c < CPL / 2; ++c) {
-            const float ck0 = cst[kc0 + lane * CPL + 2 * c], ck1 = cst[kc0 + lane * CPL + 2 * c + 1];
+        for (int q = 0; q < P_DS * P_BM / P_THREADS; ++q) {     // descriptors, transposed
+            const int i = tid + q * P_THREADS;
+            const int r = i / P_DS, dd = i % P_DS, d = d0 + dd;
+            const int64_t row = row0 + r;
+            const bool ok = row < rows && d < D;
+            cp_async<4>(bX + dd * XS + r, ok ? X + row * D + d : X, ok);
+        }
+        cp_async_commit();
+    };
+    issue(0, 0);
+
+    uint64_t acc[8][CPL / 2];   // component pairs
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < CPL / 2; ++c) acc[r][c] = 0ull;
+    for (int ph = 0; ph < nphase; ++ph) {
+        const int b = ph & 1;
+        if (ph + 1 < nphase) issue(ph + 1, b ^ 1);
+        else cp_async_commit();   // an empty group keeps the wait count uniform
+        cp_async_wait1();         // this phase's copies (of this thread) have landed
+        __syncthreads();          // ... and every thread's
+        const float *sS = smem + b * STAGE, *sN = sS + P_DS * KC, *sX = sN + P_DS * KC;
+#pragma unroll 4
+        for (int dd = 0; dd < P_DS; ++dd) {
+            const float4 xa = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8]);
+            const float4 xb = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8 + 4]);
+            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+            float sv[CPL], nv[CPL];
+            if constexpr (CPL == 4) {
+                const float4 a = *reinterpret_cast<const float4 *>(&sS[dd * KC + lane * 4]);
+                const float4 c = *reinterpret_cast<const float4 *>(&sN[dd * KC + lane * 4]);
+                sv[0] = a.x; sv[1] = a.y; sv[2] = a.z; sv[3] = a.w;
+                nv[0] = c.x; nv[1] = c.y; nv[2] = c.z; nv[3] = c.w;
+            } else {
+                const float2 a = *reinterpret_cast<const float2 *>(&sS[dd * KC + lane * 2]);
+                const float2 c = *reinterpret_cast<const float2 *>(&sN[dd * KC + lane * 2]);
+                sv[0] = a.x; sv[1] = a.y;
+                nv[0] = c.x; nv[1] = c.y;
+            }
+            uint64_t s2[CPL / 2], n2[CPL / 2];
+#pragma unroll
+            for (int c = 0; c < CPL / 2; ++c) {
+                s2[c] = pk2(sv[2 * c], sv[2 * c + 1]);
+                n2[c] = pk2(nv[2 * c], nv[2 * c + 1]);
+            }
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                float a0, a1;
-                up2(acc[r][c], a0, a1);
-                sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c] = fmaf(-0.5f, a0, ck0);
-                sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c + 1] = fmaf(-0.5f, a1, ck1);
+                const uint64_t x2 = pk2(xv[r], xv[r]);
+#pragma unroll
+                for (int c = 0; c < CPL / 2; ++c) {
+                    const uint64_t t = fma2(x2, s2[c], n2[c]);
+                    acc[r][c] = fma2(t, t, acc[r][c]);
+                }
             }
         }
+        if (ph % nslice == nslice - 1) {   // chunk done: l = c' - dist/2
+            const int kc0 = (ph / nslice) * KC;
+#pragma unroll
+            for (int c = 0; c < CPL / 2; ++c) {
+                const float ck0 = cst[kc0 + lane * CPL + 2 * c], ck1 = cst[kc0 + lane * CPL + 2 * c + 1];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    float a0, a1;
+                    up2(acc[r][c], a0, a1);
+                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c] = fmaf(-0.5f, a0, ck0);
+                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c + 1] = fmaf(-0.5f, a1, ck1);
+                    acc[r][c] = 0ull;
+                }
+            }
+        }
+        __syncthreads();   // the stage is consumed before it is refilled (and sL is complete at the end)
     }
-    __syncthreads();
 
     // row softmax: each warp owns its 8 rows
     for (int r = 0; r < 8; ++r) {
@@ -193,19 +207,6 @@ constexpr int S_DPT = 8;   // dimensions per thread
 constexpr int S_THREADS = (S_KC / S_CPT) * (S_DC / S_DPT);  // 128
 
 constexpr int S_BLOCKS_PER_SM = 3;
-
-// Asynchronous global -> shared copies (cp.async): `bytes` of 4 or 16, zero
-// fill when !valid (the source is then not read; a valid address is passed).
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // grid.x = statistics units (row ranges), grid.y = 64-component chunks,
 // grid.z = 64-dimension chunks. Stages of 32 rows are double-buffered in
@@ -334,7 +335,7 @@ cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows,
     const int Kp = g->Kp;
     const int cpl = (Kp % 128 == 0) ? 4 : 2;
     const int KC = 32 * cpl;
-    const size_t smem = sizeof(float) * (2 * P_DS * KC + P_DS * (P_BM + 4) + (size_t)P_BM * Kp);
+    const size_t smem = sizeof(float) * (2 * (2 * P_DS * KC + P_DS * (P_BM + 4)) + (size_t)P_BM * Kp);
     const unsigned grid = (unsigned)((rows + P_BM - 1) / P_BM);
     cudaError_t e;
     if (cpl == 4) {
