@@ -3,6 +3,7 @@
 // Posteriors (Algorithm 1 first loop; the paper's Phase 1, Algorithm 2):
 //   l_ik = c'_k - 1/2 sum_d t_ikd^2,  t_ikd = x_id/sigma_kd - mu_kd/sigma_kd
 //   gamma_ik = exp(l_ik - max_k l_ik) / sum_k exp(l_ik - max_k l_ik)
+// (evaluated in base 2 on y = l log2(e))
 // computed for a 64-row block against every component with register tiles of
 // 8 rows x CPL components per thread (t is one FMA, t^2 accumulation another,
 // both on component pairs with packed f32x2 instructions),
@@ -62,6 +63,14 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool vali
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+constexpr float kLog2eF = 1.4426950408889634f;
+// 2^x (ex2.approx: relative error about 2^-22, far inside the FP32 form's tolerance)
+__device__ __forceinline__ float ex2f_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 constexpr int P_BM = 64;   // rows per posterior block
 constexpr int P_DS = 16;   // dimension slice staged in shared memory
@@ -157,17 +166,17 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
                 }
             }
         }
-        if (ph % nslice == nslice - 1) {   // chunk done: l = c' - dist/2
+        if (ph % nslice == nslice - 1) {   // chunk done: y = (c' - dist/2) log2(e)
             const int kc0 = (ph / nslice) * KC;
 #pragma unroll
             for (int c = 0; c < CPL / 2; ++c) {
-                const float ck0 = cst[kc0 + lane * CPL + 2 * c], ck1 = cst[kc0 + lane * CPL + 2 * c + 1];
+                const float ck0 = cst[kc0 + lane * CPL + 2 * c] * kLog2eF, ck1 = cst[kc0 + lane * CPL + 2 * c + 1] * kLog2eF;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     float a0, a1;
                     up2(acc[r][c], a0, a1);
-                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c] = fmaf(-0.5f, a0, ck0);
-                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c + 1] = fmaf(-0.5f, a1, ck1);
+                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c] = fmaf(-0.5f * kLog2eF, a0, ck0);
+                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c + 1] = fmaf(-0.5f * kLog2eF, a1, ck1);
                     acc[r][c] = 0ull;
                 }
             }
@@ -175,27 +184,36 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
         __syncthreads();   // the stage is consumed before it is refilled (and sL is complete at the end)
     }
 
-    // row softmax: each warp owns its 8 rows
+    // row softmax in base 2: each warp owns its 8 rows, a lane holds up to 16
+    // of a row's values in registers (Kp <= 512)
     for (int r = 0; r < 8; ++r) {
         const int lr = warp * 8 + r;
         const int64_t row = row0 + lr;
         if (row >= rows) break;
-        float *L = sL + (size_t)lr * Kp;
+        const float *L = sL + (size_t)lr * Kp;
+        const int nk = Kp >> 5;
+        float v[16];
         float m = -INFINITY;
-        for (int k = lane; k < Kp; k += 32) m = fmaxf(m, L[k]);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            v[j] = j < nk ? L[lane + 32 * j] : -INFINITY;
+            m = fmaxf(m, v[j]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         float z = 0.f;
-        for (int k = lane; k < Kp; k += 32) {
-            const float e = expf(L[k] - m);
-            L[k] = e;
-            z += e;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            v[j] = j < nk ? ex2f_approx(v[j] - m) : 0.f;
+            z += v[j];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
         const float iz = 1.0f / z;
         float *G = gamma + row * Kp;
-        for (int k = lane; k < Kp; k += 32) G[k] = L[k] * iz;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nk) G[lane + 32 * j] = v[j] * iz;
     }
 }
 
