@@ -309,7 +309,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
                 rc = cuda_fail(e, "f32 posteriors launch");
                 break;
             }
-            if ((e = launch_f32_stats(g, (const float *)Xd, gam, und, nslots, part, P, st)) != cudaSuccess) {
+            if ((e = launch_f32_stats(g, (const float *)Xd, gam, und, nslots, part, P, st, true)) != cudaSuccess) {
                 rc = cuda_fail(e, "f32 statistics launch");
                 break;
             }
@@ -328,7 +328,8 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
         }
         int max_slots = 1;
         for (const FrameInfo &fi : plan.frames) max_slots = std::max(max_slots, fi.nslots);
-        if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd, nullptr, max_slots)) != cudaSuccess) {
+        if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd, nullptr, max_slots, true)) !=
+            cudaSuccess) {
             rc = cuda_fail(e, "finalise launch");
             break;
         }

@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(256)
 finalize_r_kernel(float *__restrict__ part, int P, int Kp, bool split, const FrameInfo *__restrict__ frames,
                   const int *__restrict__ B_dev) {
     __shared__ float red[8][32];
+    pdl_wait();      // the statistics slots are complete
+    pdl_trigger();
     const int f = blockIdx.z;
     if (B_dev && f >= *B_dev) return;
     const FrameInfo fr = frames[f];
@@ -99,6 +101,8 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
                   GmmDev g, double *__restrict__ sq, float *__restrict__ out, const int *__restrict__ B_dev) {
     __shared__ float tile[2][32][9];   // [u|v][component][dimension]
     __shared__ float red[FA_THREADS];
+    pdl_wait();      // the frame totals are complete
+    pdl_trigger();
     const int f = blockIdx.z;
     if (B_dev && f >= *B_dev) return;   // graph replay with fewer frames than the grid
     const int k0 = blockIdx.x * 32, d0 = blockIdx.y * 8;
@@ -160,6 +164,7 @@ __global__ void __launch_bounds__(FB_THREADS)
 finalize_b_kernel(int K, int D, int nb, const double *__restrict__ sq, float *__restrict__ out,
                   const uint32_t *__restrict__ err, const int *__restrict__ B_dev) {
     __shared__ float red[FB_THREADS];
+    pdl_wait();      // the encoded values and block squares are complete
     const int f = blockIdx.y;
     if (B_dev && f >= *B_dev) return;
     // fixed-order FP32 tree over the frame's block sums (no FP64 on the hot path)
@@ -199,38 +204,34 @@ finalize_b_kernel(int K, int D, int nb, const double *__restrict__ sq, float *__
 
 cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments, const FrameInfo *frames,
                             int B, double *sq, float *out, cudaStream_t st, const uint32_t *err, const int *B_dev,
-                            int max_slots) {
+                            int max_slots, bool pdl) {
     if (B <= 0) return cudaSuccess;
+    cudaError_t e;
     {
         // the split only changes which warps do the work, not the order
         const bool split = max_slots >= 16;
         const int J = split ? 1 : 8;
         KernelTimer kt_("finalize_r", st);
-        finalize_r_kernel<<<dim3((unsigned)((P + J - 1) / J), (unsigned)(g->Kp / 32), (unsigned)B), 256, 0, st>>>(
-            part, P, g->Kp, split, frames, B_dev);
+        e = launch_pdl(pdl, finalize_r_kernel, dim3((unsigned)((P + J - 1) / J), (unsigned)(g->Kp / 32), (unsigned)B),
+                       dim3(256), 0, st, part, P, g->Kp, split, frames, B_dev);
     }
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nbx = g->Kp / 32, nby = (g->D + 7) / 8, nb = nbx * nby;
     dim3 grid_a((unsigned)nbx, (unsigned)nby, (unsigned)B);
-    if (raw_moments) {
+    {
         KernelTimer kt_("finalize_a", st);
-        finalize_a_kernel<true><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out,
-                                                                B_dev);
-    } else {
-        KernelTimer kt_("finalize_a", st);
-        finalize_a_kernel<false><<<grid_a, FA_THREADS, 0, st>>>(part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out,
-                                                                 B_dev);
+        e = launch_pdl(pdl, raw_moments ? finalize_a_kernel<true> : finalize_a_kernel<false>, grid_a, dim3(FA_THREADS),
+                       0, st, (const float *)part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out, B_dev);
     }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     {
         KernelTimer kt_("finalize_b", st);
         const size_t n = (size_t)2 * g->K * g->D;
         const unsigned nbb = (unsigned)((n + FB_THREADS * 4 - 1) / (FB_THREADS * 4));
-        finalize_b_kernel<<<dim3(nbb, (unsigned)B), FB_THREADS, 0, st>>>(g->K, g->D, nb, sq, out, err, B_dev);
+        e = launch_pdl(pdl, finalize_b_kernel, dim3(nbb, (unsigned)B), dim3(FB_THREADS), 0, st, g->K, g->D, nb,
+                       (const double *)sq, out, err, B_dev);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace fv

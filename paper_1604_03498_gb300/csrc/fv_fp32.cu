@@ -94,6 +94,7 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
     extern __shared__ __align__(16) float smem[];
     float *sL = smem + 2 * STAGE;
 
+    pdl_trigger();   // the statistics kernel may start launching (it waits for this grid)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t row0 = (int64_t)blockIdx.x * P_BM;
     const int nslice = (D + P_DS - 1) / P_DS, nphase = (Kp / KC) * nslice;
@@ -238,6 +239,8 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     __shared__ __align__(16) float sG[2][S_RS * S_KC];
     __shared__ __align__(16) float sXs[2][S_RS * S_DC];
 
+    pdl_wait();      // the posteriors are complete
+    pdl_trigger();
     const StatUnit u = units[blockIdx.x];
     const int kc0 = blockIdx.y * S_KC, dc0 = blockIdx.z * S_DC;
     const int tid = threadIdx.x;
@@ -377,19 +380,15 @@ cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows,
 }
 
 cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
-                             int n_units, float *part, int P, cudaStream_t st) {
+                             int n_units, float *part, int P, cudaStream_t st, bool pdl) {
     if (n_units <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_units, (unsigned)(g->Kp / S_KC), (unsigned)((g->D + S_DC - 1) / S_DC));
     // 16-byte copies need 16-byte aligned rows of X (gamma rows always are)
     const bool vec = (g->D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     {
         KernelTimer kt_("f32_stats", st);
-        if (vec)
-            f32_stats_kernel<true><<<grid, S_THREADS, 0, st>>>(X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units,
-                                                               part, P);
-        else
-            f32_stats_kernel<false><<<grid, S_THREADS, 0, st>>>(X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units,
-                                                                part, P);
+        return launch_pdl(pdl, vec ? f32_stats_kernel<true> : f32_stats_kernel<false>, grid, dim3(S_THREADS), 0, st, X,
+                          g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units, part, P);
     }
     return cudaGetLastError();
 }

@@ -108,10 +108,35 @@ void build_balanced_plan(const int64_t *offsets, int B, int G, std::vector<Frame
 // ---- kernels' host launchers --------------------------------------------------
 cudaError_t launch_prep(const fv_gmm *g, const float *w, const float *mu, const float *var, cudaStream_t st);
 
+// Programmatic dependent launch (PDL): a kernel launched with launch_pdl may
+// begin while the previous kernel on the stream is still running; it calls
+// pdl_wait() before it reads anything that kernel writes (griddepcontrol.wait
+// returns once the previous grid has completed and its memory is visible; it
+// is a no-op for a normal launch). pdl_trigger() lets the next PDL kernel
+// start launching early. The first kernel of a call is always launched
+// normally, so nothing of a previous call can overlap it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma,
                                   cudaStream_t st);
 cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
-                             int n_units, float *part, int P, cudaStream_t st);
+                             int n_units, float *part, int P, cudaStream_t st, bool pdl = false);
 
 // Statistics slots are component-fastest: part[slot][j][Kp], j < P.
 // Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,
@@ -126,6 +151,7 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 // output element becomes NaN so a failed encode can never look valid.
 cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments,
                             const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
-                            const uint32_t *err = nullptr, const int *B_dev = nullptr, int max_slots = 1);
+                            const uint32_t *err = nullptr, const int *B_dev = nullptr, int max_slots = 1,
+                            bool pdl = false);
 
 }  // namespace fv
