@@ -84,6 +84,7 @@ struct Stage {
 };
 thread_local Stage t_stage;
 thread_local uint32_t t_err_word = 0;   // device error word copied back by host-output calls
+thread_local std::vector<char> t_wl;      // host image of a call's work list
 
 // Copy `bytes` from host `src` to device `dst` on `st` through a pinned slot.
 cudaError_t stage_upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
@@ -264,11 +265,15 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     const size_t o_xb = (bf16 && !x_bf16 && rows > 0) ? s.take(sizeof(uint16_t) * rows * ldx_dev) : 0;
     const size_t o_gam = !bf16 ? s.take(sizeof(float) * std::max<int64_t>(rows, 1) * Kp) : 0;
     const size_t o_part = s.take(sizeof(float) * std::max(nslots, 1) * (size_t)Kp * P);
-    const size_t o_fr = s.take(sizeof(FrameInfo) * B);
-    const size_t o_un = s.take(sizeof(StatUnit) * std::max(nslots, 1));
-    const size_t o_cta = s.take(sizeof(int2) * std::max(nctas, 1));
+    // the work list (frames, units, shares) and the zeroed error word go up
+    // in one staged copy
+    const size_t wl_fr = 0;
+    const size_t wl_un = round_up64((int64_t)(wl_fr + sizeof(FrameInfo) * B), 16);
+    const size_t wl_cta = round_up64((int64_t)(wl_un + sizeof(StatUnit) * std::max(nslots, 1)), 16);
+    const size_t wl_err = round_up64((int64_t)(wl_cta + sizeof(int2) * std::max(nctas, 1)), 16);
+    const size_t wl_bytes = wl_err + 16;
+    const size_t o_wl = s.take(wl_bytes);
     const size_t o_sq = s.take(sizeof(double) * (size_t)B * (Kp / 32) * ((D + 7) / 8));
-    const size_t o_err = s.take(sizeof(uint32_t));
     const size_t o_out = !out_on_device ? s.take(sizeof(float) * fvlen * B) : 0;
     cudaError_t e = cudaMallocAsync((void **)&s.base, s.off, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
@@ -287,22 +292,23 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
             Xd = s.base + o_x;
         }
         float *outd = out_on_device ? fv_out : (float *)(s.base + o_out);
-        FrameInfo *frd = (FrameInfo *)(s.base + o_fr);
-        StatUnit *und = (StatUnit *)(s.base + o_un);
-        int2 *ctad = (int2 *)(s.base + o_cta);
-        if ((e = stage_upload(frd, plan.frames.data(), sizeof(FrameInfo) * B, st)) != cudaSuccess ||
-            (e = stage_upload(und, plan.units.data(), sizeof(StatUnit) * nslots, st)) != cudaSuccess ||
-            (e = stage_upload(ctad, plan.cta.data(), sizeof(int2) * nctas, st)) != cudaSuccess) {
-            rc = cuda_fail(e, "work-list upload");
-            break;
+        FrameInfo *frd = (FrameInfo *)(s.base + o_wl + wl_fr);
+        StatUnit *und = (StatUnit *)(s.base + o_wl + wl_un);
+        int2 *ctad = (int2 *)(s.base + o_wl + wl_cta);
+        uint32_t *errd = (uint32_t *)(s.base + o_wl + wl_err);
+        {
+            std::vector<char> &h = t_wl;
+            h.assign(wl_bytes, 0);
+            std::memcpy(h.data() + wl_fr, plan.frames.data(), sizeof(FrameInfo) * B);
+            std::memcpy(h.data() + wl_un, plan.units.data(), sizeof(StatUnit) * nslots);
+            std::memcpy(h.data() + wl_cta, plan.cta.data(), sizeof(int2) * nctas);
+            if ((e = stage_upload(s.base + o_wl, h.data(), wl_bytes, st)) != cudaSuccess) {
+                rc = cuda_fail(e, "work-list upload");
+                break;
+            }
         }
         float *part = (float *)(s.base + o_part);
         double *sq = (double *)(s.base + o_sq);
-        uint32_t *errd = (uint32_t *)(s.base + o_err);
-        if ((e = cudaMemsetAsync(errd, 0, sizeof(uint32_t), st)) != cudaSuccess) {
-            rc = cuda_fail(e, "cudaMemsetAsync(error word)");
-            break;
-        }
         if (!bf16) {
             float *gam = (float *)(s.base + o_gam);
             if ((e = launch_f32_posteriors(g, (const float *)Xd, rows, gam, st)) != cudaSuccess) {
