@@ -159,40 +159,50 @@ enum {
     EB_XCHG = 17,     // [2] peers' (max, sum) of a tile arrived, by bytes (slot = tile parity)
     EB_HXFULL = 19,   // [4] both column halves of a quadrant's rows have written (max, sum)
     EB_HXFREE = 23,   // [4] both halves have read them
-    EB_NBARS = 27
+    EB_XRFREE = 27,   // the builders hold a tile's x in registers: the landing buffer may refill
+    EB_NBARS = 28
 };
 
-// Y planes of one tile: x copied from the landing buffer, x^2 split into hi
-// and lo, and the ones block. Rows past the unit's end (the next frame, or
-// zero fill) are zeroed in every plane, so they add nothing to the
-// statistics whatever their posteriors. Thread t of nt.
-__device__ __forceinline__ void build_y(uint8_t *sy, const uint8_t *xr, uint32_t plane, int nkb, int valid, int t,
-                                        int nt) {
-    const int chunks = nkb * kRows * 2;   // 16-byte chunks of the x plane
-    for (int c0 = t; c0 < chunks; c0 += 4 * nt) {
-        uint4 x[4];
+// Y planes of one tile, built in two steps so that only the stores wait for
+// the stage to come free. x_load reads thread t's 16-byte chunks of the x
+// block from the landing buffer into registers (every supported D fits:
+// 3*D16 + 16 <= 256 columns gives at most 5 column blocks, 1280 chunks, i.e.
+// kHold chunks per builder thread); y_store writes x, the hi and lo halves of
+// x^2 and the ones block. Rows past the unit's end (the next frame, or zero
+// fill) are zeroed in every plane, so they add nothing to the statistics
+// whatever their posteriors.
+constexpr int kBuilders = 192;
+constexpr int kHold = (5 * kRows * 2 + kBuilders - 1) / kBuilders;
+
+__device__ __forceinline__ void x_load(uint4 (&x)[kHold], const uint8_t *xr, int nkb, int t) {
+    const int chunks = nkb * kRows * 2;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)   // four loads in flight before any store
-            if (c0 + u * nt < chunks) x[u] = *reinterpret_cast<const uint4 *>(xr + (c0 + u * nt) * 16);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int c = c0 + u * nt;
-            if (c >= chunks) break;
-            const int row = (c >> 1) & (kRows - 1);   // 32-byte rows; the swizzle stays inside a row
-            uint4 hi, lo;
-            if (row < valid) {
-                square_split(x[u], hi, lo);
-            } else {
-                x[u] = make_uint4(0u, 0u, 0u, 0u);
-                hi = x[u];
-                lo = x[u];
-            }
-            *reinterpret_cast<uint4 *>(sy + c * 16) = x[u];
-            *reinterpret_cast<uint4 *>(sy + plane + c * 16) = hi;
-            *reinterpret_cast<uint4 *>(sy + 2 * plane + c * 16) = lo;
-        }
+    for (int u = 0; u < kHold; ++u) {
+        const int c = t + u * kBuilders;
+        if (c < chunks) x[u] = *reinterpret_cast<const uint4 *>(xr + c * 16);
     }
-    for (int c = t; c < kRows * 2; c += nt) {
+}
+
+__device__ __forceinline__ void y_store(uint8_t *sy, uint4 (&x)[kHold], uint32_t plane, int nkb, int valid, int t) {
+    const int chunks = nkb * kRows * 2;
+#pragma unroll
+    for (int u = 0; u < kHold; ++u) {
+        const int c = t + u * kBuilders;
+        if (c >= chunks) break;
+        const int row = (c >> 1) & (kRows - 1);   // 32-byte rows; the swizzle stays inside a row
+        uint4 hi, lo;
+        if (row < valid) {
+            square_split(x[u], hi, lo);
+        } else {
+            x[u] = make_uint4(0u, 0u, 0u, 0u);
+            hi = x[u];
+            lo = x[u];
+        }
+        *reinterpret_cast<uint4 *>(sy + c * 16) = x[u];
+        *reinterpret_cast<uint4 *>(sy + plane + c * 16) = hi;
+        *reinterpret_cast<uint4 *>(sy + 2 * plane + c * 16) = lo;
+    }
+    for (int c = t; c < kRows * 2; c += kBuilders) {
         const uint32_t one = (c >> 1) < valid ? 0x3F803F80u : 0u;   // bf16 1.0 pairs
         *reinterpret_cast<uint4 *>(sy + 3 * plane + c * 16) = make_uint4(one, one, one, one);
     }
@@ -267,6 +277,7 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             mbar_init(&bars[EB_HXFULL + q], 64);
             mbar_init(&bars[EB_HXFREE + q], 64);
         }
+        mbar_init(&bars[EB_XRFREE], 6);
         misc[1] = 0u;
         fence_mbar_init();
     }
@@ -285,9 +296,9 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA loads and log-likelihood GEMMs ----------------
-        // Tile i's Y planes built (AFULL) also frees the landing buffer, so
-        // x of tile i + 1 is requested then; L(i) follows once its TMEM
-        // buffer is free. (Issuing L blocks this thread for most of its
+        // The builders taking tile i's x into registers (XRFREE) frees the
+        // landing buffer, so x of tile i + 1 is requested then; L(i) follows
+        // once tile i's Y planes are built (AFULL) and its TMEM buffer is free. (Issuing L blocks this thread for most of its
         // duration, so the statistics GEMMs have their own thread.)
         prefetch_tmap(&tmX);
         prefetch_tmap(&tmB);
@@ -314,11 +325,12 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         bool issued = false;
         for (int i = 0; ok && w.more(); w.next(), ++i) {
             const int s = i % p.nstage, b = i & 1;
-            if (!mbar_wait(&bars[EB_AFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
+            if (!mbar_wait(&bars[EB_XRFREE], i & 1, abort_flag, p.err)) break;
             if (wn.more()) {
                 load_x(i + 1, wn.row0());
                 wn.next();
             }
+            if (!mbar_wait(&bars[EB_AFULL + s], (i / p.nstage) & 1, abort_flag, p.err)) break;
             if (i >= 2 && !mbar_wait(&bars[EB_LEMPTY + b], ((i >> 1) - 1) & 1, abort_flag, p.err)) break;
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + L.y + s * L.y_stage);
@@ -379,14 +391,18 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         }
     } else if (warp == 2 || warp == 3 || warp >= 12) {
         // ---------------- Y builders: the tile's Y planes from the landing buffer ----------------
-        const int bt = (warp < 12 ? warp - 2 : warp - 10) * 32 + lane;   // 0..191
+        const int bt = (warp < 12 ? warp - 2 : warp - 10) * 32 + lane;   // 0..kBuilders-1
         int i = 0;
         for (TileWalk w(p.units, cu); w.more(); w.next(), ++i) {
             const int s = i % p.nstage, j = i - p.nstage;   // tile j used this stage before
             if (!mbar_wait(&bars[EB_XRFULL + (i & 1)], (i >> 1) & 1, abort_flag, p.err)) break;
+            uint4 x[kHold];
+            x_load(x, smem + L.xr, p.nkb, bt);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars[EB_XRFREE]);   // release: the reads precede the next TMA write
             if (j >= 0 && !mbar_wait(&bars[EB_STFREE + (j & 1)], (j >> 1) & 1, abort_flag, p.err)) break;
-            build_y(smem + L.y + s * L.y_stage, smem + L.xr, plane, p.nkb, w.valid(), bt, 192);
-            fence_proxy_async_smem();   // also orders the landing-buffer reads before its next TMA write
+            y_store(smem + L.y + s * L.y_stage, x, plane, p.nkb, w.valid(), bt);
+            fence_proxy_async_smem();   // generic-proxy stores visible to the MMAs
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars[EB_AFULL + s]);
         }
@@ -645,7 +661,8 @@ bool enc_config(const fv_gmm *g, EncCfg &c) {
     c.ny = 3 * c.nkb * 16 + 16;
     c.nstage = enc_smem(c.nkb, c.S, 2).total <= (uint32_t)kMaxSmem ? 2 : 1;
     c.smem = enc_smem(c.nkb, c.S, c.nstage).total;
-    return g->Kp % kComps == 0 && c.S >= 1 && c.S <= 4 && c.ny <= 256 && c.smem <= (size_t)kMaxSmem;
+    return g->Kp % kComps == 0 && c.S >= 1 && c.S <= 4 && c.ny <= 256 && c.nkb * kRows * 2 <= kHold * kBuilders &&
+           c.smem <= (size_t)kMaxSmem;
 }
 
 void enc_launch_config(const EncCfg &c, int clusters, cudaStream_t st, cudaLaunchConfig_t &cfg,
