@@ -274,8 +274,8 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         mbar_init(&bars[EB_TEMPTY], 8);
         mbar_init(&bars[EB_DRAIN], 1);
         for (int q = 0; q < 4; ++q) {
-            mbar_init(&bars[EB_HXFULL + q], 64);
-            mbar_init(&bars[EB_HXFREE + q], 64);
+            mbar_init(&bars[EB_HXFULL + q], 2);   // one arrive per warp, after __syncwarp
+            mbar_init(&bars[EB_HXFREE + q], 2);
         }
         mbar_init(&bars[EB_XRFREE], 6);
         misc[1] = 0u;
@@ -496,10 +496,12 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             if (i > 0 && !__all_sync(0xffffffffu, mbar_wait(&bars[EB_HXFREE + q], (i - 1) & 1, abort_flag, p.err)))
                 break;
             hx[h * kRows + r] = make_float2(m, z);
-            mbar_arrive(&bars[EB_HXFULL + q]);
+            __syncwarp();   // the warp's writes ordered before its one (release) arrive
+            if (lane == 0) mbar_arrive(&bars[EB_HXFULL + q]);
             if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_HXFULL + q], i & 1, abort_flag, p.err))) break;
             const float2 h0 = hx[r], h1 = hx[kRows + r];
-            mbar_arrive(&bars[EB_HXFREE + q]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars[EB_HXFREE + q]);
             float mh, zh;
             {
                 mh = fmaxf(h0.x, h1.x);
@@ -508,12 +510,16 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             }
             // (max, sum) over the cluster, combined in rank order so that every
             // CTA normalises with the same value. Exchange slot i % 2 of every
-            // CTA receives the peers' values for tile i by st.async (counted in
-            // bytes on XCHG, armed once per tile); warps 4-7 send. A peer
-            // writes slot i % 2 again only for tile i + 2, after this CTA's
-            // contribution to tile i + 1, which warps 4-7 send only after the
-            // half handshake of tile i + 1, i.e. after warps 8-11 have read
-            // tile i's values.
+            // CTA receives the peers' values for tile i (counted in bytes on
+            // XCHG, armed once per tile); warps 4-7 write their 32 rows into
+            // their own rank's segment of the slot and send it to each peer as
+            // one 256-byte bulk copy. A peer writes slot i % 2 again only for
+            // tile i + 2, after this CTA's contribution to tile i + 1, which
+            // warps 4-7 send only after the half handshake of tile i + 1, i.e.
+            // after warps 8-11 have read tile i's values; likewise this CTA
+            // rewrites its own segment (the copies' source) for tile i + 2 only
+            // after every peer's tile i + 1 values arrived, which they send
+            // after tile i's copies from here have landed.
             float M = -INFINITY, Z = 0.f;
             if (p.S > 1) {
                 const int j = i & 1;
@@ -521,10 +527,13 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                 if (h == 0) {
                     if (q == 0 && lane == 0)
                         mbar_arrive_expect_tx(&bars[EB_XCHG + j], (uint32_t)(p.S - 1) * kRows * 8u);
-                    for (int pr = 0; pr < p.S; ++pr) {
-                        if (pr == (int)rank) continue;
-                        st_async_f32x2(mapa(smem_u32(&xb[rank * kRows + r]), (uint32_t)pr), mh, zh,
-                                       mapa(smem_u32(&bars[EB_XCHG + j]), (uint32_t)pr));
+                    xb[rank * kRows + r] = make_float2(mh, zh);
+                    fence_proxy_async_smem();   // the copy engine reads what the lanes wrote
+                    __syncwarp();
+                    if (lane < p.S && lane != (int)rank) {   // lane pr sends to peer pr
+                        const uint32_t seg = smem_u32(&xb[rank * kRows + q * 32]);
+                        bulk_s2cluster(mapa(seg, (uint32_t)lane), seg, 32u * 8u,
+                                       mapa(smem_u32(&bars[EB_XCHG + j]), (uint32_t)lane));
                     }
                 }
                 if (!__all_sync(0xffffffffu,

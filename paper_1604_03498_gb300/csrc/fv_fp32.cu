@@ -134,29 +134,36 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
         cp_async_wait1();         // this phase's copies (of this thread) have landed
         __syncthreads();          // ... and every thread's
         const float *sS = smem + b * STAGE, *sN = sS + P_DS * KC, *sX = sN + P_DS * KC;
-#pragma unroll 4
-        for (int dd = 0; dd < P_DS; ++dd) {
-            const float4 xa = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8]);
-            const float4 xb = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8 + 4]);
-            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-            float sv[CPL], nv[CPL];
+        // the shared-memory operands of slice dd + 1 are loaded into
+        // registers while slice dd is computed (the loads' latency is hidden)
+        float4 pxa, pxb;
+        float pv[2 * CPL];   // CPL scale values, then CPL offsets
+        auto load = [&](int dd) {
+            pxa = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8]);
+            pxb = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8 + 4]);
             if constexpr (CPL == 4) {
                 const float4 a = *reinterpret_cast<const float4 *>(&sS[dd * KC + lane * 4]);
                 const float4 c = *reinterpret_cast<const float4 *>(&sN[dd * KC + lane * 4]);
-                sv[0] = a.x; sv[1] = a.y; sv[2] = a.z; sv[3] = a.w;
-                nv[0] = c.x; nv[1] = c.y; nv[2] = c.z; nv[3] = c.w;
+                pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
+                pv[4] = c.x; pv[5] = c.y; pv[6] = c.z; pv[7] = c.w;
             } else {
                 const float2 a = *reinterpret_cast<const float2 *>(&sS[dd * KC + lane * 2]);
                 const float2 c = *reinterpret_cast<const float2 *>(&sN[dd * KC + lane * 2]);
-                sv[0] = a.x; sv[1] = a.y;
-                nv[0] = c.x; nv[1] = c.y;
+                pv[0] = a.x; pv[1] = a.y;
+                pv[2] = c.x; pv[3] = c.y;
             }
+        };
+        load(0);
+#pragma unroll
+        for (int dd = 0; dd < P_DS; ++dd) {
+            const float xv[8] = {pxa.x, pxa.y, pxa.z, pxa.w, pxb.x, pxb.y, pxb.z, pxb.w};
             uint64_t s2[CPL / 2], n2[CPL / 2];
 #pragma unroll
             for (int c = 0; c < CPL / 2; ++c) {
-                s2[c] = pk2(sv[2 * c], sv[2 * c + 1]);
-                n2[c] = pk2(nv[2 * c], nv[2 * c + 1]);
+                s2[c] = pk2(pv[2 * c], pv[2 * c + 1]);
+                n2[c] = pk2(pv[CPL + 2 * c], pv[CPL + 2 * c + 1]);
             }
+            if (dd + 1 < P_DS) load(dd + 1);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const uint64_t x2 = pk2(xv[r], xv[r]);
@@ -301,13 +308,19 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
         if (active) {
             const float *G = sG[buf];
             const float *Xs = sXs[buf];
+            // the operands of row r + 1 are loaded while row r is accumulated
+            float4 g4 = *reinterpret_cast<const float4 *>(&G[cg * S_CPT]);
+            float4 xa = *reinterpret_cast<const float4 *>(&Xs[dl]);
+            float4 xb = *reinterpret_cast<const float4 *>(&Xs[dl + 4]);
 #pragma unroll 4
             for (int r = 0; r < S_RS; ++r) {
-                const float4 g4 = *reinterpret_cast<const float4 *>(&G[r * S_KC + cg * S_CPT]);
-                const float4 xa = *reinterpret_cast<const float4 *>(&Xs[r * S_DC + dl]);
-                const float4 xb = *reinterpret_cast<const float4 *>(&Xs[r * S_DC + dl + 4]);
                 const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
                 const uint64_t xv[4] = {pk2(xa.x, xa.y), pk2(xa.z, xa.w), pk2(xb.x, xb.y), pk2(xb.z, xb.w)};
+                if (r + 1 < S_RS) {
+                    g4 = *reinterpret_cast<const float4 *>(&G[(r + 1) * S_KC + cg * S_CPT]);
+                    xa = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl]);
+                    xb = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl + 4]);
+                }
 #pragma unroll
                 for (int c = 0; c < S_CPT; ++c) {
                     S0[c] += gv[c];

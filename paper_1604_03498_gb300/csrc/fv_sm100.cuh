@@ -315,6 +315,17 @@ __device__ __forceinline__ void st_async_f32x2(uint32_t cluster_addr, float a, f
                  "f"(a), "f"(b), "r"(cluster_bar)
                  : "memory");
 }
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from this CTA's shared memory to a peer's, counted in bytes on the peer's
+// mbarrier. dst and bar are cluster addresses (mapa); src a CTA address whose
+// generic-proxy writes were fenced with fence_proxy_async_smem.
+__device__ __forceinline__ void bulk_s2cluster(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
+                                               uint32_t cluster_bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_cluster),
+                 "r"(src_cta), "r"(bytes), "r"(cluster_bar)
+                 : "memory");
+}
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
