@@ -519,6 +519,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-threads", type=int, default=4,
+                    help="host threads (each with its own stream) of the end-to-end measurement")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the simulated 64-stream serving trace (the workload's full length is 60)")
     ap.add_argument("--config", choices=["c1", "c3"], default=None,
@@ -668,7 +670,7 @@ def main():
     # before it returns (a host-output call synchronises its stream); E2E_THREADS host threads,
     # each with its own CUDA stream, encode interleaved frames so one frame's copies overlap
     # another's kernels (ctypes releases the GIL during a call).
-    E2E_THREADS = 4
+    E2E_THREADS = max(1, args.e2e_threads)
     Xh = torch.from_numpy(np.stack(frames)).pin_memory()
     outh = torch.zeros(POOL, 2 * KD).pin_memory()
     e2e_steps = max(1, min(args.steps, 20))

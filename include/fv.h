@@ -103,6 +103,19 @@ FV_API void fv_gmm_free(fv_gmm *gmm);
 /* Report K, D and precision of a loaded GMM (any pointer may be NULL). */
 FV_API int fv_gmm_info(const fv_gmm *gmm, int *K, int *D, int *precision);
 
+/* The per-component constants of the log-likelihood as the loader computed
+ * them on the device in FP64 (Sec. 3.1, Algorithm 1: the constant part of the
+ * log posterior, log prior plus the Gaussian's normaliser; the -D/2 log 2pi
+ * term is common to every component and left out):
+ *   c_direct[k]   = log w_k - 1/2 sum_d log sigma^2_kd          (w renormalised to sum 1)
+ *   c_expanded[k] = c_direct[k] - 1/2 sum_d mu_kd^2 / sigma^2_kd
+ * The FP32 form uses c_direct with the centred distance, the BF16 form
+ * c_expanded with the expanded [x, x^2] product; both are rounded to FP32
+ * from these values. Host arrays of K doubles owned by the caller, either may
+ * be NULL. Synchronous (waits for the load to finish). FV_ERR_INVALID on a
+ * NULL handle, FV_ERR_CUDA if the copy fails. */
+FV_API int fv_gmm_constants(const fv_gmm *gmm, double *c_direct, double *c_expanded);
+
 /* Largest K and D the given precision supports. */
 FV_API int fv_limits(fv_precision precision, int *max_K, int *max_D);
 

@@ -48,6 +48,8 @@ def _load():
             lib.fvo_encode.restype = ctypes.c_int
             lib.fvo_encode.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        P, P, P, P, ctypes.c_double, P, P, P, P, P, P]
+            lib.fvo_log_constants.restype = ctypes.c_int
+            lib.fvo_log_constants.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
             _lib = lib
     return _lib
 
@@ -88,3 +90,16 @@ def encode(X, w, mu, var, tau: float = 0.0, want_gamma: bool = False, want_stats
     if want_stats:
         out.update(U=U, V=V, S0=S0)
     return out
+
+
+def log_constants(w, var):
+    """Step 1's constant of every component, log w_k - 1/2 sum_d log var_kd
+    (Algorithm 1), in FP64; returns an array of K values."""
+    lib = _load()
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+    var = np.ascontiguousarray(var, dtype=np.float64)
+    K, D = var.shape
+    cst = np.zeros(K)
+    st = lib.fvo_log_constants(D, K, _p(w), _p(var), _p(cst))
+    assert st == 0, st
+    return cst

@@ -45,6 +45,20 @@
 #define FVO_BADARG 2
 #define FVO_NOMEM 3
 
+/* Step 1's per-component constant of the log posterior,
+ *   c_k = log w_k - 1/2 sum_d log sigma^2_kd
+ * (Algorithm 1: the prior and the Gaussian normaliser; the -D/2 log 2pi term
+ * is common to every component and cancels in the posteriors). */
+int fvo_log_constants(int D, int K, const double *w, const double *var, double *cst) {
+    if (D <= 0 || K <= 0 || !w || !var || !cst) return FVO_BADARG;
+    for (int k = 0; k < K; ++k) {
+        double slog = 0.0;
+        for (int d = 0; d < D; ++d) slog += log(var[(int64_t)k * D + d]);
+        cst[k] = log(w[k]) - 0.5 * slog;
+    }
+    return FVO_OK;
+}
+
 int fvo_encode(int64_t N, int D, int K,
                const double *X,    /* N x D, row-major */
                const double *w,    /* K priors */
@@ -77,14 +91,8 @@ int fvo_encode(int64_t N, int D, int K,
     }
 
     /* Step 1: sqrt(sigma^-1), i.e. 1/sigma, and the per-component constant. */
-    for (int k = 0; k < K; ++k) {
-        double slog = 0.0;
-        for (int d = 0; d < D; ++d) {
-            isd[(int64_t)k * D + d] = 1.0 / sqrt(var[(int64_t)k * D + d]);
-            slog += log(var[(int64_t)k * D + d]);
-        }
-        cst[k] = log(w[k]) - 0.5 * slog;
-    }
+    for (int64_t j = 0; j < KD; ++j) isd[j] = 1.0 / sqrt(var[j]);
+    fvo_log_constants(D, K, w, var, cst);
 
     /* Steps 2-3: posteriors of every descriptor (first phase). */
     for (int64_t i = 0; i < N; ++i) {

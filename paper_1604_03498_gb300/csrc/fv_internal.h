@@ -69,6 +69,9 @@ struct GmmDev {
     uint16_t *bimg;
     float *cfull;    // [Kp] log w - 1/2 sum log sigma^2 - 1/2 sum mu^2/sigma^2 (FP64 -> FP32; -inf on padding)
     float *cl2;      // [Kp] cfull * log2(e), formed in FP64
+    // the same constants before rounding: [0, Kp) log w - 1/2 sum log sigma^2,
+    // [Kp, 2 Kp) minus 1/2 sum mu^2/sigma^2 (FP64; -inf on padding)
+    double *c64;
 };
 
 }  // namespace fv

@@ -70,6 +70,8 @@ __global__ void prep_kernel(int K, int D, int Kp, int Dp, int D16, const float *
                 for (int t = 0; t < 4; ++t) g.bimg[((size_t)t * Kp + k) * D16 + d] = 0;
         if (threadIdx.x == 0) {
             g.cst[k] = -INFINITY;
+            g.c64[k] = -INFINITY;
+            g.c64[Kp + k] = -INFINITY;
             if (g.cfull) g.cfull[k] = -INFINITY;
             if (g.cl2) g.cl2[k] = -INFINITY;
             g.alpha[k] = 0.f;
@@ -118,6 +120,8 @@ __global__ void prep_kernel(int K, int D, int Kp, int Dp, int D16, const float *
         const double wk = (double)w[k] / ws;
         const double c1 = log(wk) - 0.5 * slog;
         g.cst[k] = (float)c1;
+        g.c64[k] = c1;
+        g.c64[Kp + k] = c1 - 0.5 * smq;
         if (g.cfull) g.cfull[k] = (float)(c1 - 0.5 * smq);
         if (g.cl2) g.cl2[k] = (float)((c1 - 0.5 * smq) * 1.4426950408889634);
         g.alpha[k] = (float)(1.0 / sqrt(wk));
@@ -194,7 +198,7 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
     const size_t o_s_t = take(sizeof(float) * D * Kp), o_nms_t = take(sizeof(float) * D * Kp);
-    const size_t o_cst = take(sizeof(float) * Kp);
+    const size_t o_cst = take(sizeof(float) * Kp), o_c64 = take(sizeof(double) * 2 * Kp);
     const size_t o_s_kd = take(sizeof(float) * Kp * Dp), o_mu_kd = take(sizeof(float) * Kp * Dp);
     const size_t o_alpha = take(sizeof(float) * Kp), o_beta = take(sizeof(float) * Kp);
     const size_t o_mu = take(sizeof(float) * D * Kp), o_prec = take(sizeof(float) * D * Kp);
@@ -217,6 +221,7 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     d.s_t = (float *)(base + o_s_t);
     d.nms_t = (float *)(base + o_nms_t);
     d.cst = (float *)(base + o_cst);
+    d.c64 = (double *)(base + o_c64);
     d.s_kd = (float *)(base + o_s_kd);
     d.mu_kd = (float *)(base + o_mu_kd);
     d.alpha = (float *)(base + o_alpha);
@@ -259,6 +264,20 @@ extern "C" void fv_gmm_free(fv_gmm *g) {
     cudaFree(g->block);
     if (cur != g->device) cudaSetDevice(cur);
     delete g;
+}
+
+extern "C" int fv_gmm_constants(const fv_gmm *g, double *c_direct, double *c_expanded) {
+    if (!g) return fail(FV_ERR_INVALID, "fv_gmm_constants: NULL handle");
+    if (c_direct) {
+        const cudaError_t e = cudaMemcpy(c_direct, g->dev.c64, sizeof(double) * g->K, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "fv_gmm_constants: copy");
+    }
+    if (c_expanded) {
+        const cudaError_t e =
+            cudaMemcpy(c_expanded, g->dev.c64 + g->Kp, sizeof(double) * g->K, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "fv_gmm_constants: copy");
+    }
+    return FV_OK;
 }
 
 extern "C" int fv_gmm_info(const fv_gmm *g, int *K, int *D, int *precision) {

@@ -83,6 +83,8 @@ def lib():
             L.fv_gmm_free.restype = None
             L.fv_gmm_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
             L.fv_gmm_info.restype = I
+            L.fv_gmm_constants.argtypes = [P, P, P]
+            L.fv_gmm_constants.restype = I
             L.fv_limits.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I)]
             L.fv_limits.restype = I
             L.fv_encode.argtypes = [P, P, I64, I, P, I, P]
@@ -203,6 +205,16 @@ def fv_gmm_load(weights, means, variances, precision: int = FV_PREC_FP32) -> Gmm
 
 def fv_gmm_free(g: Gmm) -> None:
     g.close()
+
+
+def fv_gmm_constants(g: Gmm):
+    """C fv_gmm_constants: the FP64 per-component constants (c_direct,
+    c_expanded) the loader computed on the device, as two arrays of K."""
+    K, _, _ = fv_gmm_info(g)
+    cd = np.zeros(K)
+    ce = np.zeros(K)
+    _check(lib().fv_gmm_constants(g.handle, cd.ctypes.data, ce.ctypes.data))
+    return cd, ce
 
 
 def fv_gmm_info(g: Gmm):

@@ -115,3 +115,30 @@ def test_bf16_empty_input():
     st, out = gpu_encode(P, np.zeros((0, 16), np.float32), w, mu, var)
     assert st == fv.FV_ERR_EMPTY
     assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("K,D", [(256, 64), (512, 64), (512, 80)])
+def test_bf16_repeated_calls_are_bitwise_identical(K, D):
+    """Sixteen 320x240-shaped frames in one call, repeated: every repeat gives
+    the same bits (the cluster exchanges, the stage and TMEM hand-offs and
+    the slot reduction leave no order-dependent result), and frames sampled
+    from the batch match the oracle."""
+    torch = torch_cuda()
+    _, w, mu, var = case(K, D, 10, 34)
+    F, N = 16, 19200
+    frames = [synth.sample_descriptors(w, mu, var, N, seed=400 + i, gmm_frac=0.8) for i in range(F)]
+    g = fv.fv_gmm_load(w, mu, var, P)
+    X = torch.from_numpy(np.concatenate(frames)).cuda().to(torch.bfloat16)
+    offs = [i * N for i in range(F + 1)]
+    out = torch.zeros(F, 2 * K * D, device="cuda")
+    fv.fv_encode_batch_bf16(g, X, D, offs, out)
+    torch.cuda.synchronize()
+    ref = out.clone()
+    for _ in range(12):
+        fv.fv_encode_batch_bf16(g, X, D, offs, out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    g.close()
+    got = ref.cpu().numpy()
+    for f in (0, F - 1):
+        assert max_err(got[f], oracle_fv(_rounded(frames[f]), w, mu, var)) <= TOL[P]
