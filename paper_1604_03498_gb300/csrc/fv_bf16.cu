@@ -36,10 +36,11 @@
 // swizzle (TMA writes it; read K-major by the first GEMM and MN-major by the
 // second); gamma^T in 64-component blocks with the 128-byte swizzle.
 //
-// Warp roles (16 warps): 0 TMA producer, 1 MMA issuer, 2-3 and 12-15 build
-// each tile's Y planes (x copied from the TMA landing buffer, x^2 split,
-// ones) while the softmax of the previous tile runs, 4-11 softmax (two warps
-// per TMEM lane quadrant, one per 64-component half, on every tile).
+// Warp roles (16 warps): 0 TMA loads and the log-likelihood MMAs, 1 the
+// statistics MMAs, 2-3 and 12-15 build each tile's Y planes (x taken from the
+// TMA landing buffer into registers, x^2 split, ones) while the softmax of
+// the previous tile runs, 4-11 softmax (two warps per TMEM lane quadrant, one
+// per 64-component half, on every tile).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
