@@ -209,6 +209,28 @@ __device__ __forceinline__ void y_store(uint8_t *sy, uint4 (&x)[kHold], uint32_t
     }
 }
 
+// A softmax warp's share of a unit's statistics, TMEM -> slot (see the
+// flush in the kernel). Not inlined: it runs once per unit, and keeping it
+// out of the kernel body leaves the tile loop's code as it is.
+__device__ __noinline__ void write_stats(uint32_t ts, float *stg, float *dst0, int h, int P, int Kp, int lane) {
+    for (int n0 = h * 32; n0 < P; n0 += 64) {
+        uint32_t va[32];
+        tmem_ld32_issue(ts + n0, va);
+        tmem_ld_wait(va);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) stg[e * 32 + lane] = __uint_as_float(va[e]);
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int row = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
+            if (n0 + row < P)
+                *reinterpret_cast<float4 *>(dst0 + (size_t)(n0 + row) * Kp + c4) =
+                    *reinterpret_cast<const float4 *>(stg + row * 32 + c4);
+        }
+        __syncwarp();   // the block is read before the next group overwrites it
+    }
+}
+
 // Walks a cluster's units tile by tile (the current unit is held in registers).
 struct TileWalk {
     const StatUnit *u;
@@ -592,19 +614,15 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             // columns follow the TMEM columns ([S1 | S2hi | S2lo] blocks of
             // D16, then S0, the first ones column), so this is a copy; warps
             // 4-7 take 32-column groups 0, 2, ..., warps 8-11 groups 1, 3, ...
+            // Each group goes through the warp's own 4 KB of the gamma^T
+            // buffer (its pass-B rows, free until its next pass B): lane c
+            // writes its component's 32 values as column c of a [32 j][32 c]
+            // block, then each lane stores 16 bytes (4 components) of one j
+            // row, so one warp store covers four 128-byte row pieces.
             if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_SDONE], uidx & 1, abort_flag, p.err))) break;
             tc_fence_after();
-            const int k = (int)rank * kComps + r;
-            float *dst = p.part + (size_t)uslot * p.Kp * p.P + k;
-            const uint32_t ts = lane_base + kStatCol;
-            for (int n0 = h * 32; n0 < p.P; n0 += 64) {
-                uint32_t va[32];
-                tmem_ld32_issue(ts + n0, va);
-                tmem_ld_wait(va);
-#pragma unroll
-                for (int e = 0; e < 32; ++e)
-                    if (n0 + e < p.P) dst[(size_t)(n0 + e) * p.Kp] = __uint_as_float(va[e]);
-            }
+            write_stats(lane_base + kStatCol, reinterpret_cast<float *>(smem + L.g + h * kGHalf + q * 32 * 128),
+                        p.part + (size_t)uslot * p.Kp * p.P + (size_t)rank * kComps + q * 32, h, p.P, p.Kp, lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars[EB_TEMPTY]);
