@@ -251,7 +251,12 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     const StatUnit u = units[blockIdx.x];
     const int kc0 = blockIdx.y * S_KC, dc0 = blockIdx.z * S_DC;
     const int tid = threadIdx.x;
-    const int cg = tid & 15, dg = tid >> 4;
+    // warp w takes components 16w..16w+15 over all 64 dimensions (lanes:
+    // 4 component groups x 8 dimension groups), so a row whose posteriors
+    // are exactly zero for those 16 components can be skipped by the whole
+    // warp: it would add exact zeros (the FP32 exponential underflows for
+    // every component far from the descriptor)
+    const int cg = (tid >> 5) * 4 + (tid & 3), dg = (tid & 31) >> 2;
     const int kb = kc0 + cg * S_CPT, dl = dg * S_DPT, db = dc0 + dl;
     const bool active = db < D;
 
@@ -305,7 +310,7 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
         else cp_async_commit();   // an empty group keeps the wait count uniform
         cp_async_wait1();         // this stage's copies (of this thread) have landed
         __syncthreads();          // ... and every thread's
-        if (active) {
+        {
             const float *G = sG[buf];
             const float *Xs = sXs[buf];
             // the operands of row r + 1 are loaded while row r is accumulated
@@ -321,6 +326,8 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
                     xa = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl]);
                     xb = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl + 4]);
                 }
+                const bool nz = (gv[0] != 0.f) | (gv[1] != 0.f) | (gv[2] != 0.f) | (gv[3] != 0.f);
+                if (!__any_sync(0xffffffffu, nz)) continue;   // exact zeros for all 16 components
 #pragma unroll
                 for (int c = 0; c < S_CPT; ++c) {
                     S0[c] += gv[c];
