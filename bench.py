@@ -39,7 +39,7 @@ K_COMP, D_DIM, N_DESC = 256, 64, 19200
 POOL = 64
 # independent frames are issued round-robin on this many CUDA streams (measured best: the FP32
 # form's kernels leave SMs idle and gain up to 8; the BF16 encoder fills every SM and gains at 2)
-FRAME_STREAMS = 8
+FRAME_STREAMS = 16
 FRAME_STREAMS_BF16 = 2
 GMM_SEED = 0
 METRIC = "FV descriptors/sec (320x240-shaped frames, N=19200, D=64, K=256)"
@@ -519,7 +519,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--e2e-threads", type=int, default=4,
+    ap.add_argument("--frame-streams", type=int, default=FRAME_STREAMS,
+                    help="CUDA streams the FP32 per-frame headline issues its frames on")
+    ap.add_argument("--e2e-threads", type=int, default=6,
                     help="host threads (each with its own stream) of the end-to-end measurement")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the simulated 64-stream serving trace (the workload's full length is 60)")
@@ -565,11 +567,12 @@ def main():
     out = torch.zeros(POOL, 2 * KD, device="cuda")
 
     # ---- plain FP32 form, one frame per call (the headline) ----
-    # Frames are independent: a step issues its 64 calls round-robin on FRAME_STREAMS CUDA
+    # Frames are independent: a step issues its 64 calls round-robin on --frame-streams CUDA
     # streams forked from and joined back into the timed stream, so one frame's kernels fill the
     # tails of another's. The single-stream time is reported beside it.
     g32 = fv.fv_gmm_load(w, mu, var, fv.FV_PREC_FP32)
-    fstreams = [torch.cuda.Stream() for _ in range(max(FRAME_STREAMS, FRAME_STREAMS_BF16))]
+    nfs = max(1, args.frame_streams)
+    fstreams = [torch.cuda.Stream() for _ in range(max(nfs, FRAME_STREAMS_BF16))]
 
     def fork_join(issue, n):
         ev = torch.cuda.Event()
@@ -587,8 +590,8 @@ def main():
             fv.fv_encode(g32, Xd[f], out[f], stream=stream.cuda_stream, allow=(fv.FV_OK,))
 
     def step32():
-        fork_join(lambda: [fv.fv_encode(g32, Xd[f], out[f], stream=fstreams[f % FRAME_STREAMS].cuda_stream,
-                                        allow=(fv.FV_OK,)) for f in range(POOL)], FRAME_STREAMS)
+        fork_join(lambda: [fv.fv_encode(g32, Xd[f], out[f], stream=fstreams[f % nfs].cuda_stream,
+                                        allow=(fv.FV_OK,)) for f in range(POOL)], nfs)
 
     for _ in range(warm):
         step32()
@@ -713,7 +716,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD + " (plain FP32 form)", "frames_per_step": POOL,
                        "frames_per_s": value / N_DESC, "us_per_frame": 1e3 * ms / (args.steps * POOL),
-                       "frame_streams": FRAME_STREAMS,
+                       "frame_streams": nfs,
                        "single_stream_value": world * args.steps * POOL * N_DESC / (ms1 / 1e3),
                        "single_stream_us_per_frame": 1e3 * ms1 / (args.steps * POOL),
                        "l2": "inputs larger than L2: 64-frame pool = 315 MB FP32 / 157 MB bf16",
