@@ -642,10 +642,17 @@ def main():
     issued_bf = {"bf16_encode": 2.0 * K_COMP * 5 * D16 + 2.0 * K_COMP * (3 * D16 + 16)}
     forms = {}
     for name, stepf, frames_per_call in (("bf16", step_bf, 1), ("bf16_batched", step_bf_batch, POOL)):
-        for _ in range(warm):
-            stepf()
-        torch.cuda.synchronize()
-        msb, lb = timed(stepf, args.steps, stream, barrier, dist)
+        # one-frame calls: the encoder grid fills the GPU, so whether a second stream helps depends on
+        # how the two calls' kernels interleave; both are timed and the faster one is the value
+        variants = [(1, step_bf_1), (FRAME_STREAMS_BF16, stepf)] if name == "bf16" else [(1, stepf)]
+        per_streams = {}
+        for ns, fn in variants:
+            for _ in range(warm):
+                fn()
+            torch.cuda.synchronize()
+            per_streams[ns] = timed(fn, args.steps, stream, barrier, dist)
+        best = min(per_streams, key=lambda ns: per_streams[ns][0])
+        msb, lb = per_streams[best]
         # per-kernel times on one stream (concurrent streams would inflate each launch's time)
         prof = kernel_times(step_bf_1 if name == "bf16" else stepf, max(1, args.steps // 4))
         rows_per_launch = N_DESC * frames_per_call
@@ -655,7 +662,9 @@ def main():
                            workload="frame" if frames_per_call == 1 else "batch64")
         vb = world * args.steps * POOL * N_DESC / (msb / 1e3)
         forms[name] = {"value": vb, "unit": "descriptors/s", "frames_per_s": vb / N_DESC,
-                       "frame_streams": FRAME_STREAMS_BF16 if name == "bf16" else 1,
+                       "frame_streams": best,
+                       "us_per_frame_by_streams": {str(ns): 1e3 * v[0] / (args.steps * POOL)
+                                                   for ns, v in per_streams.items()},
                        "us_per_frame": 1e3 * msb / (args.steps * POOL), "frames_per_call": frames_per_call,
                        "ms_per_step": msb / args.steps, "gpu_launches": lb, "roofline": roof,
                        "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / max(1, v[0])}
