@@ -180,15 +180,24 @@ def run_reference(args):
 
 
 # ---- measured traffic of a kernel (from a committed ncu summary) ------------------
+def code_hash(src: str) -> str:
+    """sha256 prefix of a CUDA source with its comments and blank lines
+    removed, so that editing a comment does not orphan a measurement."""
+    text = open(src).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()[:12]
+
+
 def measured_traffic(kernel: str, source: str, workload: str):
     """DRAM bytes per launch recorded in profiles/traffic.md for `kernel` on
     `workload` ("frame" or "batch64"), valid only while the kernel's source
-    file still has the hash recorded there."""
+    file still has the code hash (code_hash) recorded there."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     src = os.path.join(ROOT, "paper_1604_03498_gb300", "csrc", source)
     if not (os.path.exists(path) and os.path.exists(src)):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    sha = code_hash(src)
     for ln in open(path):
         m = re.match(r"\|\s*(\S+)\s*\|\s*(\w+)\s*\|\s*([0-9.eE+]+)\s*\|\s*(\w+)\s*\|", ln)
         if m and m.group(1) == kernel and m.group(2) == sha and m.group(4) == workload:

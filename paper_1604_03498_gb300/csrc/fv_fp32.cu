@@ -18,9 +18,13 @@
 // The residual x - mu carries a rounding error relative to itself; the
 // posteriors' single-FMA form x/sigma - mu/sigma errs by ~eps |mu/sigma|, which
 // is harmless inside a softmax but would be amplified near zero by the signed
-// square root when a component's variance is tiny. Every block writes its own
-// statistics slot; the finalise kernel reduces the slots in a fixed order, so
-// no atomics touch the result.
+// square root when a component's variance is tiny. Terms whose posterior is
+// exactly zero (the FP32 exponential underflows for every component far from
+// the descriptor, most of them in 64 dimensions) add exact zeros, so a warp
+// skips a row when all its components' posteriors are zero: the sums are
+// bitwise those of the dense loop. Every block writes its own statistics slot;
+// the finalise kernel reduces the slots in a fixed order, so no atomics touch
+// the result.
 #include "fv_internal.h"
 
 namespace fv {
