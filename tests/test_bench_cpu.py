@@ -28,3 +28,21 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_rows_follow_code_not_comments(tmp_path):
+    """profiles/traffic.md rows are keyed by a hash of the kernel source
+    without comments: editing a comment keeps a measurement, editing code
+    drops it."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(float *x) {\n  x[0] = 1.f;  // one\n}\n")
+    b = tmp_path / "b.cu"
+    b.write_text("/* a different\n   header */\n__global__ void k(float *x) {\n  x[0] = 1.f;\n\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("// header\n__global__ void k(float *x) {\n  x[0] = 2.f;  // one\n}\n")
+    assert bench.code_hash(str(a)) == bench.code_hash(str(b))
+    assert bench.code_hash(str(a)) != bench.code_hash(str(c))
