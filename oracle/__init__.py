@@ -3,10 +3,12 @@
 TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the benchmark's
 CPU-baseline leg may import this package; the product path never does.
 
-The arithmetic lives in ``fv_oracle.c`` (paper Sec. 3.1, Algorithm 1, plus
-the improved-FV normalisation of Sec. 4). This module compiles it with the
-host C compiler, loads it with ctypes and converts arrays. Every parity pin
-of the oracle is in the oracle tests; no function here is "parity unpinned".
+The arithmetic lives in ``fv_oracle.c`` (paper Sec. 3.1: the GMM
+log-likelihoods, the posteriors and the U, V statistics of Algorithm 1, stated
+from their definitions; plus the improved-FV normalisation of Sec. 4). This
+module compiles it with the host C compiler, loads it with ctypes and converts
+arrays. Every parity pin of the oracle is in the oracle tests; no function
+here is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -38,34 +40,51 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _bind(lib):
+    P = ctypes.c_void_p
+    lib.fvo_encode.restype = ctypes.c_int
+    lib.fvo_encode.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                               P, P, P, P, ctypes.c_double, P, P, P, P, P, P]
+    lib.fvo_log_constants.restype = ctypes.c_int
+    lib.fvo_log_constants.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
+    lib.fvo_log_likelihoods.restype = ctypes.c_int
+    lib.fvo_log_likelihoods.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+    lib.fvo_posteriors.restype = ctypes.c_int
+    lib.fvo_posteriors.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_SO)
-            P = ctypes.c_void_p
-            lib.fvo_encode.restype = ctypes.c_int
-            lib.fvo_encode.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int,
-                                       P, P, P, P, ctypes.c_double, P, P, P, P, P, P]
-            lib.fvo_log_constants.restype = ctypes.c_int
-            lib.fvo_log_constants.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_SO))
     return _lib
+
+
+def load_variant(src: str, out_dir: str):
+    """Compile another copy of the oracle source (the tests plant mistakes
+    in copies to check that the pins catch them) and return its bound
+    library, for the ``lib`` argument of encode()."""
+    so = os.path.join(out_dir, os.path.basename(src) + ".so")
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                           "-ffp-contract=off", src, "-o", so, "-lm"])
+    return _bind(ctypes.CDLL(so))
 
 
 def _p(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def encode(X, w, mu, var, tau: float = 0.0, want_gamma: bool = False, want_stats: bool = False):
+def encode(X, w, mu, var, tau: float = 0.0, want_gamma: bool = False, want_stats: bool = False, lib=None):
     """Encode one descriptor set. Inputs are converted to float64 (exactly).
 
     Returns a dict with ``fv`` (2KD, normalised), ``fv_raw`` (2KD, before the
     signed square root and L2 step), ``status``, and optionally ``gamma``
     (N x K), ``U``, ``V`` (K x D, unscaled sums) and ``S0`` (K).
     """
-    lib = _load()
+    lib = lib or _load()
     X = np.ascontiguousarray(X, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
@@ -103,3 +122,31 @@ def log_constants(w, var):
     st = lib.fvo_log_constants(D, K, _p(w), _p(var), _p(cst))
     assert st == 0, st
     return cst
+
+
+def log_likelihoods(X, w, mu, var):
+    """The N x K matrix L_ik = log w_k + log N(x_i; mu_k, sigma^2_k) + (D/2) log 2pi."""
+    lib = _load()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    var = np.ascontiguousarray(var, dtype=np.float64)
+    K, D = mu.shape
+    N = X.shape[0]
+    L = np.zeros((max(N, 1), K))
+    st = lib.fvo_log_likelihoods(N, D, K, _p(X), _p(w), _p(mu), _p(var), _p(L))
+    assert st == 0, st
+    return L[:N]
+
+
+def posteriors(X, w, mu, var):
+    """(gamma N x K, lse N): the posteriors and the per-descriptor
+    log-sum-exp lse_i = log sum_k exp(L_ik), i.e. log p(x_i) + (D/2) log 2pi."""
+    lib = _load()
+    L = log_likelihoods(X, w, mu, var)
+    N, K = L.shape
+    g = np.zeros((max(N, 1), K))
+    lse = np.zeros(max(N, 1))
+    st = lib.fvo_posteriors(N, K, _p(np.ascontiguousarray(L if N else np.zeros((1, K)))), _p(g), _p(lse))
+    assert st == 0, st
+    return g[:N], lse[:N]

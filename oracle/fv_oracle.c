@@ -6,34 +6,34 @@
  * leg of the benchmark may load it; the product library never does, and it
  * shares no code, header or constant with the CUDA sources.
  *
- * Method (paper Sec. 3.1, Algorithm 1, "Fisher Vector Encoding Algorithm"),
- * followed step by step in the paper's order:
- *   1. precompute 1/sqrt(sigma^2) per component and dimension
- *      (the "compute sqrt(sigma^-1)" step; the paper's "covariances" are
- *      the diagonal variances sigma^2);
- *   2. per descriptor i and component k: distance
- *        d_ik = sum_d ((x_id - mu_kd) / sigma_kd)^2
- *      (centred form, no expansion), log-posterior with the prior
- *        l_ik = log w_k - 1/2 sum_d log sigma^2_kd - 1/2 d_ik
- *      (the -D/2 log 2pi term is common to all k and cancels), and the
- *      running maximum over k;
- *   3. gamma_ik = exp(l_ik - max_k l_ik) / sum_k exp(l_ik - max_k l_ik);
- *   4. for every (i, k) with gamma_ik > tau and every d, with
- *      t = (x_id - mu_kd) / sigma_kd:
- *        U_kd += gamma_ik * t,   V_kd += gamma_ik * (t^2 - 1);
- *      tau = 0 keeps every term (the exact encoding); the paper's
- *      early-termination threshold (Sec. 3.3, Algorithm 5) is 1e-6;
- *   5. the improved-FV scaling of the encoding scheme the paper adopts
- *      (Sec. 4, "the same encoding scheme as VLFeat"):
- *        u_kd = U_kd / (N sqrt(w_k)),   v_kd = V_kd / (N sqrt(2 w_k));
- *   6. z = [u_0 .. u_{K-1}, v_0 .. v_{K-1}] (each block D-contiguous),
- *      z_j <- sign(z_j) sqrt(|z_j|), z <- z / ||z||_2 (left as zeros when
- *      the norm is zero).
+ * What it computes, stated from the definitions (paper Sec. 3.1 and the
+ * encoding scheme adopted in Sec. 4, improved Fisher vectors of FV-ijcv13):
  *
- * All arithmetic is IEEE double with libm exp/log/sqrt. Parity pins for every
- * step live in the oracle tests (posteriors against a library mixture model,
- * U/V against autograd gradients of the log-likelihood, K=1 and
- * identical-component closed forms, invariances, hard assignment).
+ *   log-likelihood matrix (Sec. 3.1: a diagonal-covariance GMM with priors
+ *   w_k, means mu_k and "covariances" sigma^2_k):
+ *     L_ik = log w_k + log N(x_i; mu_k, diag sigma^2_k) + (D/2) log 2pi
+ *          = log w_k - 1/2 sum_d log sigma^2_kd
+ *                    - 1/2 sum_d (x_id - mu_kd)^2 / sigma^2_kd
+ *     (the (D/2) log 2pi term is common to every component and cancels);
+ *   posteriors (Bayes' rule, the "posteriors" of Algorithm 1):
+ *     gamma_ik = exp(L_ik - lse_i),  lse_i = log sum_k exp(L_ik),
+ *     with lse_i evaluated around the row maximum so nothing overflows;
+ *   gradient statistics (Sec. 3.1, the U and V of Algorithm 1), with the
+ *   standardised residual t_ikd = (x_id - mu_kd) / sigma_kd:
+ *     U_kd = sum_i gamma_ik t_ikd,   V_kd = sum_i gamma_ik (t_ikd^2 - 1),
+ *     S0_k = sum_i gamma_ik, each sum over the terms with gamma_ik > tau
+ *     (tau = 0 keeps every term: the exact encoding; the paper's early
+ *     termination threshold, Sec. 3.3, is 1e-6);
+ *   encoding (Sec. 4, "the same encoding scheme as VLFeat"):
+ *     u_kd = U_kd / (N sqrt(w_k)),  v_kd = V_kd / (N sqrt(2 w_k)),
+ *     z = [u_0 .. u_{K-1}, v_0 .. v_{K-1}] (each block D-contiguous),
+ *     z_j <- sign(z_j) sqrt|z_j|,  z <- z / ||z||_2 (zeros stay zeros).
+ *
+ * All arithmetic is IEEE double with libm exp/log/sqrt, one definition per
+ * function. Parity pins for every function live in the oracle tests
+ * (posteriors against a library mixture model, U/V against autograd
+ * gradients of the log-likelihood, K=1 and identical-component closed forms,
+ * invariances, hard assignment, brute force in 50-digit decimal).
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,10 +45,7 @@
 #define FVO_BADARG 2
 #define FVO_NOMEM 3
 
-/* Step 1's per-component constant of the log posterior,
- *   c_k = log w_k - 1/2 sum_d log sigma^2_kd
- * (Algorithm 1: the prior and the Gaussian normaliser; the -D/2 log 2pi term
- * is common to every component and cancels in the posteriors). */
+/* The component-only part of L_ik: log w_k - 1/2 sum_d log sigma^2_kd. */
 int fvo_log_constants(int D, int K, const double *w, const double *var, double *cst) {
     if (D <= 0 || K <= 0 || !w || !var || !cst) return FVO_BADARG;
     for (int k = 0; k < K; ++k) {
@@ -59,6 +56,111 @@ int fvo_log_constants(int D, int K, const double *w, const double *var, double *
     return FVO_OK;
 }
 
+/* The N x K log-likelihood matrix L (definition above), row-major. */
+int fvo_log_likelihoods(int64_t N, int D, int K, const double *X, const double *w, const double *mu,
+                        const double *var, double *L) {
+    if (N < 0 || D <= 0 || K <= 0 || !X || !w || !mu || !var || !L) return FVO_BADARG;
+    double *cst = (double *)malloc(sizeof(double) * K);
+    double *prec = (double *)malloc(sizeof(double) * (size_t)K * D);   /* 1 / sigma^2 */
+    if (!cst || !prec) {
+        free(cst);
+        free(prec);
+        return FVO_NOMEM;
+    }
+    fvo_log_constants(D, K, w, var, cst);
+    for (int64_t j = 0; j < (int64_t)K * D; ++j) prec[j] = 1.0 / var[j];
+    for (int64_t i = 0; i < N; ++i) {
+        for (int k = 0; k < K; ++k) {
+            double q = 0.0;   /* squared Mahalanobis distance of x_i from mu_k */
+            for (int d = 0; d < D; ++d) {
+                const double r = X[i * D + d] - mu[(int64_t)k * D + d];
+                q += r * r * prec[(int64_t)k * D + d];
+            }
+            L[i * K + k] = cst[k] - 0.5 * q;
+        }
+    }
+    free(cst);
+    free(prec);
+    return FVO_OK;
+}
+
+/* gamma = exp(L - lse) row by row; lse_out (N, nullable) receives lse_i. */
+int fvo_posteriors(int64_t N, int K, const double *L, double *gamma, double *lse_out) {
+    if (N < 0 || K <= 0 || !L || !gamma) return FVO_BADARG;
+    for (int64_t i = 0; i < N; ++i) {
+        const double *l = L + i * K;
+        double m = -INFINITY;
+        for (int k = 0; k < K; ++k) m = l[k] > m ? l[k] : m;
+        double z = 0.0;
+        for (int k = 0; k < K; ++k) z += exp(l[k] - m);
+        const double lse = m + log(z);
+        for (int k = 0; k < K; ++k) gamma[i * K + k] = exp(l[k] - lse);
+        if (lse_out) lse_out[i] = lse;
+    }
+    return FVO_OK;
+}
+
+/* U, V (K x D) and S0 (K) from the posteriors, terms with gamma > tau. */
+int fvo_moments(int64_t N, int D, int K, const double *X, const double *mu, const double *var, const double *gamma,
+                double tau, double *U, double *V, double *S0) {
+    if (N < 0 || D <= 0 || K <= 0 || !X || !mu || !var || !gamma || !U || !V || !S0) return FVO_BADARG;
+    double *isd = (double *)malloc(sizeof(double) * D);   /* 1 / sigma of one component */
+    if (!isd) return FVO_NOMEM;
+    for (int k = 0; k < K; ++k) {
+        const double *m = mu + (int64_t)k * D;
+        double *u_k = U + (int64_t)k * D, *v_k = V + (int64_t)k * D;
+        for (int d = 0; d < D; ++d) {
+            isd[d] = 1.0 / sqrt(var[(int64_t)k * D + d]);
+            u_k[d] = v_k[d] = 0.0;
+        }
+        S0[k] = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            const double g = gamma[i * K + k];
+            if (!(g > tau)) continue;
+            S0[k] += g;
+            for (int d = 0; d < D; ++d) {
+                const double t = (X[i * D + d] - m[d]) * isd[d];
+                u_k[d] += g * t;
+                v_k[d] += g * (t * t - 1.0);
+            }
+        }
+    }
+    free(isd);
+    return FVO_OK;
+}
+
+static double signed_sqrt(double a) { return a > 0 ? sqrt(a) : (a < 0 ? -sqrt(-a) : 0.0); }
+
+/* The encoding of Sec. 4 from U, V: fv_raw = [u; v] (nullable), fv = the
+ * signed square root of it, L2-normalised. */
+int fvo_fisher_vector(int64_t N, int D, int K, const double *w, const double *U, const double *V, double *fv,
+                      double *fv_raw) {
+    if (N <= 0 || D <= 0 || K <= 0 || !w || !U || !V || !fv) return FVO_BADARG;
+    const int64_t KD = (int64_t)K * D;
+    for (int k = 0; k < K; ++k) {
+        for (int d = 0; d < D; ++d) {
+            const double u = U[(int64_t)k * D + d] / ((double)N * sqrt(w[k]));
+            const double v = V[(int64_t)k * D + d] / ((double)N * sqrt(2.0 * w[k]));
+            if (fv_raw) {
+                fv_raw[(int64_t)k * D + d] = u;
+                fv_raw[KD + (int64_t)k * D + d] = v;
+            }
+            fv[(int64_t)k * D + d] = signed_sqrt(u);
+            fv[KD + (int64_t)k * D + d] = signed_sqrt(v);
+        }
+    }
+    double nrm2 = 0.0;
+    for (int64_t j = 0; j < 2 * KD; ++j) nrm2 += fv[j] * fv[j];
+    if (nrm2 > 0.0) {
+        const double nrm = sqrt(nrm2);
+        for (int64_t j = 0; j < 2 * KD; ++j) fv[j] /= nrm;
+    }
+    return FVO_OK;
+}
+
+/* Whole encoder: descriptors and GMM in, normalised Fisher vector out.
+ * Optional outputs (nullable): fv_raw (2KD), gamma (N x K), U, V (K x D),
+ * S0 (K). N == 0 gives FVO_EMPTY and a zero vector. */
 int fvo_encode(int64_t N, int D, int K,
                const double *X,    /* N x D, row-major */
                const double *w,    /* K priors */
@@ -78,88 +180,27 @@ int fvo_encode(int64_t N, int D, int K,
     if (fv_raw) memset(fv_raw, 0, sizeof(double) * 2 * KD);
     if (N == 0) return FVO_EMPTY;
 
-    double *isd = (double *)malloc(sizeof(double) * KD);   /* 1/sigma */
-    double *cst = (double *)malloc(sizeof(double) * K);    /* log w - 1/2 sum log var */
-    double *U = (double *)calloc((size_t)KD, sizeof(double));
-    double *V = (double *)calloc((size_t)KD, sizeof(double));
-    double *S0 = (double *)calloc((size_t)K, sizeof(double));
-    double *post = gamma_out ? gamma_out : (double *)malloc(sizeof(double) * (size_t)(N * K));
-    if (!isd || !cst || !U || !V || !S0 || !post) {
-        free(isd); free(cst); free(U); free(V); free(S0);
-        if (post != gamma_out) free(post);
-        return FVO_NOMEM;
-    }
-
-    /* Step 1: sqrt(sigma^-1), i.e. 1/sigma, and the per-component constant. */
-    for (int64_t j = 0; j < KD; ++j) isd[j] = 1.0 / sqrt(var[j]);
-    fvo_log_constants(D, K, w, var, cst);
-
-    /* Steps 2-3: posteriors of every descriptor (first phase). */
-    for (int64_t i = 0; i < N; ++i) {
-        const double *x = X + i * D;
-        double *p = post + i * K;
-        double maxpost = -INFINITY;
-        for (int k = 0; k < K; ++k) {
-            double dist = 0.0;
-            for (int d = 0; d < D; ++d) {
-                double t = (x[d] - mu[(int64_t)k * D + d]) * isd[(int64_t)k * D + d];
-                dist += t * t;
-            }
-            p[k] = cst[k] - 0.5 * dist;
-            if (p[k] > maxpost) maxpost = p[k];
-        }
-        double sum = 0.0;
-        for (int k = 0; k < K; ++k) {
-            p[k] = exp(p[k] - maxpost);
-            sum += p[k];
-        }
-        for (int k = 0; k < K; ++k) p[k] = p[k] / sum;
-    }
-
-    /* Step 4: first- and second-order statistics (second phase). */
-    for (int64_t i = 0; i < N; ++i) {
-        const double *x = X + i * D;
-        const double *p = post + i * K;
-        for (int k = 0; k < K; ++k) {
-            double g = p[k];
-            if (!(g > tau)) continue;
-            S0[k] += g;
-            for (int d = 0; d < D; ++d) {
-                double t = (x[d] - mu[(int64_t)k * D + d]) * isd[(int64_t)k * D + d];
-                U[(int64_t)k * D + d] += t * g;
-                V[(int64_t)k * D + d] += (t * t - 1.0) * g;
-            }
+    double *L = (double *)malloc(sizeof(double) * (size_t)(N * K));
+    double *gam = gamma_out ? gamma_out : (double *)malloc(sizeof(double) * (size_t)(N * K));
+    double *U = (double *)malloc(sizeof(double) * KD);
+    double *V = (double *)malloc(sizeof(double) * KD);
+    double *S0 = (double *)malloc(sizeof(double) * K);
+    int rc = FVO_NOMEM;
+    if (L && gam && U && V && S0) {
+        rc = fvo_log_likelihoods(N, D, K, X, w, mu, var, L);
+        if (rc == FVO_OK) rc = fvo_posteriors(N, K, L, gam, NULL);
+        if (rc == FVO_OK) rc = fvo_moments(N, D, K, X, mu, var, gam, tau, U, V, S0);
+        if (rc == FVO_OK) rc = fvo_fisher_vector(N, D, K, w, U, V, fv, fv_raw);
+        if (rc == FVO_OK) {
+            if (U_out) memcpy(U_out, U, sizeof(double) * KD);
+            if (V_out) memcpy(V_out, V, sizeof(double) * KD);
+            if (S0_out) memcpy(S0_out, S0, sizeof(double) * K);
         }
     }
-
-    /* Step 5: improved-FV scaling; step 6: signed square root, L2. */
-    double nrm2 = 0.0;
-    for (int k = 0; k < K; ++k) {
-        double su = 1.0 / ((double)N * sqrt(w[k]));
-        double sv = 1.0 / ((double)N * sqrt(2.0 * w[k]));
-        for (int d = 0; d < D; ++d) {
-            double u = U[(int64_t)k * D + d] * su;
-            double v = V[(int64_t)k * D + d] * sv;
-            if (fv_raw) {
-                fv_raw[(int64_t)k * D + d] = u;
-                fv_raw[KD + (int64_t)k * D + d] = v;
-            }
-            double zu = (u > 0) ? sqrt(u) : ((u < 0) ? -sqrt(-u) : 0.0);
-            double zv = (v > 0) ? sqrt(v) : ((v < 0) ? -sqrt(-v) : 0.0);
-            fv[(int64_t)k * D + d] = zu;
-            fv[KD + (int64_t)k * D + d] = zv;
-            nrm2 += zu * zu + zv * zv;
-        }
-    }
-    if (nrm2 > 0.0) {
-        double inv = 1.0 / sqrt(nrm2);
-        for (int64_t j = 0; j < 2 * KD; ++j) fv[j] *= inv;
-    }
-
-    if (U_out) memcpy(U_out, U, sizeof(double) * KD);
-    if (V_out) memcpy(V_out, V, sizeof(double) * KD);
-    if (S0_out) memcpy(S0_out, S0, sizeof(double) * K);
-    free(isd); free(cst); free(U); free(V); free(S0);
-    if (post != gamma_out) free(post);
-    return FVO_OK;
+    free(L);
+    if (gam != gamma_out) free(gam);
+    free(U);
+    free(V);
+    free(S0);
+    return rc;
 }

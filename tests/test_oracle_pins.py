@@ -62,6 +62,23 @@ def test_posteriors_match_scipy_log_densities():
     np.testing.assert_allclose(g, softmax(logp, axis=1), rtol=0, atol=1e-12)
 
 
+def test_log_likelihood_matrix_and_row_normaliser_match_scipy():
+    """L_ik = log w_k + log N(x_i; mu_k, sigma^2_k) + (D/2) log 2pi and
+    lse_i = log sum_k exp(L_ik), against scipy's Gaussian log-density and
+    logsumexp (the evidence log p(x_i) up to the common 2pi term)."""
+    from scipy.special import logsumexp
+    from scipy.stats import norm
+    X, w, mu, var = _case(K=9, D=7, N=120, seed=8, frac=0.6)
+    D = X.shape[1]
+    ref = np.log(w)[None, :] + norm.logpdf(X[:, None, :], loc=mu[None], scale=np.sqrt(var)[None]).sum(-1)
+    ref += 0.5 * D * math.log(2 * math.pi)
+    L = oracle.log_likelihoods(X, w, mu, var)
+    np.testing.assert_allclose(L, ref, rtol=1e-13, atol=1e-11)
+    g, lse = oracle.posteriors(X, w, mu, var)
+    np.testing.assert_allclose(lse, logsumexp(ref, axis=1), rtol=1e-13, atol=1e-11)
+    np.testing.assert_allclose(g, oracle.encode(X, w, mu, var, want_gamma=True)["gamma"], rtol=0, atol=1e-15)
+
+
 # --- first and second order statistics --------------------------------------
 
 def test_statistics_are_loglikelihood_gradients():
