@@ -138,6 +138,23 @@ def oracle_throughput(frames, w, mu, var, seconds: float, rows: int | None = Non
     return done / dt, cores, sample
 
 
+def oracle_errors(pairs, w, mu, var, threads: int | None = None):
+    """Max-abs error of GPU vectors against the FP64 oracle on the same
+    descriptors: pairs = [(fv_gpu, X_for_oracle), ...]; run on the host
+    cores after the timed region. Returns the worst error and the count."""
+    import oracle
+    oracle.build()
+
+    def one(pair):
+        got, X = pair
+        ref = oracle.encode(X, w, mu, var)["fv"]
+        return float(np.abs(np.asarray(got, np.float64) - ref).max())
+
+    with cf.ThreadPoolExecutor(max_workers=threads or (os.cpu_count() or 1)) as ex:
+        errs = list(ex.map(one, pairs))
+    return {"max_abs_err_vs_oracle": max(errs) if errs else None, "frames_checked": len(errs)}
+
+
 def run_reference(args):
     """The oracle as the reference arm, same workload, metric and unit."""
     rank, _, world = _env_rank()
@@ -266,8 +283,8 @@ def roofline_of(prof, work, bound, peak, unit, peak_basis, source, issued=None, 
     return r
 
 
-def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, stream, barrier, dist, world, tc_peak, work_bf,
-                       issued_bf):
+def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, pool_f32, stream, barrier, dist, world, tc_peak, work_bf,
+                       issued_bf, tc_sustained):
     """256 frames with N ~ Uniform{5000..40000} (D=64, K=256, bf16 descriptors
     resident in HBM, ~737 MB) encoded per step by one fv_batch_plan_run: one
     CUDA-graph launch of the persistent kernels. Frame contents are prefixes of
@@ -304,6 +321,12 @@ def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, stream, barrier, dist,
     fv.fv_batch_plan_run(plan, offs, out)
     torch.cuda.synchronize()
     ok = bool(torch.isfinite(out).all().item()) and abs(float(out[0].norm()) - 1.0) < 1e-3
+    # error against the oracle on four sampled frames of the batch (their bf16 rows, gathered on the host)
+    flat_h = synth.to_bf16_grid(np.stack(pool_f32).reshape(-1, D_DIM))
+    pick = [int(b) for b in np.random.default_rng(4).choice(B, 4, replace=False)]
+    out_h = out.cpu().numpy()
+    err = oracle_errors([(out_h[b], flat_h[src[offs[b]:offs[b + 1]]]) for b in pick], w, mu, var)
+    err["frames"] = pick
     per_launch_ms = ms / steps
     # algorithmic tensor work of the whole graph (both GEMMs) over its launch time
     algo = work_bf["bf16_encode"] * rows
@@ -312,11 +335,13 @@ def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, stream, barrier, dist,
     r = {"value": value, "unit": "descriptors/s", "frames_per_s": world * steps * B / (ms / 1e3),
          "us_per_frame": 1e3 * ms / (steps * B), "frames_per_launch": B, "rows_per_launch": rows,
          "ms_per_graph_launch": per_launch_ms, "gpu_launches": launches, "steps": steps,
-         "frame_sizes": "Uniform{5000..40000}, seed 4", "output_finite_unit_norm": ok,
+         "frame_sizes": "Uniform{5000..40000}, seed 4", "output_finite_unit_norm": ok, "error": err,
          "autotune": {"stat_ctas": info["stat_ctas"], "tuned": info["tuned"], "tuned_ms": info["tuned_ms"],
                       "plan_create_s": create_s},
          "roofline_graph": {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                             "frac": achieved / tc_peak, "issued_frac": issued / (per_launch_ms / 1e3) / 1e12 / tc_peak,
+                            "peak_basis": "MEASURED_PEAKS bf16_tflops (burst, of measured)",
+                            "frac_of_sustained": achieved / tc_sustained,
                             "work": "both GEMMs' algorithmic flops per graph launch / graph time"}}
     plan.close()
     return r
@@ -349,6 +374,11 @@ def serving_form(args):
                               max_batch_frames=128, max_frame_descriptors=40000, batch_window_ns=0)
     fvlen = 2 * K * D
 
+    # a seeded 1% sample of the served frames is kept and checked against the oracle after the runs
+    n_sample = max(1, len(frames) // 100)
+    sample_idx = set(int(i) for i in np.random.default_rng(5).choice(len(frames), n_sample, replace=False))
+    kept = {}
+
     def replay_server(paced):
         import threading
         tickets, lat, qd, bsz = [], [], [], []
@@ -372,6 +402,8 @@ def serving_form(args):
                     time.sleep(0.0002)
                     continue
                 st, info = fv.fv_server_poll(srv, t, out, timeout_ns=60_000_000_000)
+                if paced and i in sample_idx:
+                    kept[i] = out.copy()
                 lat.append(info["latency_ns"] / 1e6)
                 qd.append(info["queue_ns"] / 1e6)
                 bsz.append(info["batch_frames"])
@@ -443,11 +475,19 @@ def serving_form(args):
     srv.close()
     gbf.close()
     g32.close()
+    # the server stores descriptors as bfloat16: the oracle gets the same rounded frames, and the
+    # original FP32 frames (input quantisation included) on the same sample
+    t0 = time.perf_counter()
+    idx = sorted(kept)
+    err = {"same_bf16_input": oracle_errors([(kept[i], synth.to_bf16_grid(frames[i])) for i in idx], w, mu, var),
+           "fp32_input": oracle_errors([(kept[i], frames[i]) for i in idx[:max(1, len(idx) // 8)]], w, mu, var),
+           "sample": f"{len(idx)} of {len(frames)} served frames (seeded 1%); FP32-input check on every 8th of them",
+           "oracle_s": time.perf_counter() - t0}
     return {"workload": f"{NS} streams x {FPS:.0f} fps x {args.serve_seconds:.0f} s, N ~ U{{8000..40000}}, "
                         f"D={D}, K={K}, 16 GB admission budget, bf16",
             "served_bf16_paced": served, "plain_fp32_paced": plain,
             "served_bf16_saturated": served_sat, "plain_fp32_saturated": plain_sat,
-            "server_stats": stats}
+            "server_stats": stats, "served_error": err}
 
 
 def ncu_case(kind: str) -> int:
@@ -532,8 +572,9 @@ def main():
                     help="CUDA streams the FP32 per-frame headline issues its frames on")
     ap.add_argument("--e2e-threads", type=int, default=6,
                     help="host threads (each with its own stream) of the end-to-end measurement")
-    ap.add_argument("--serve-seconds", type=float, default=20.0,
-                    help="length of the simulated 64-stream serving trace (the workload's full length is 60)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the simulated 64-stream serving trace (the workload's full length, 60 s; "
+                         "shorter for quick runs)")
     ap.add_argument("--config", choices=["c1", "c3"], default=None,
                     help="time one of the other workload shapes alone and exit (not the headline)")
     ap.add_argument("--ncu-case", choices=["fp32", "bf16", "bf16_batched"], default=None,
@@ -567,7 +608,11 @@ def main():
     sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 FMA lanes x 2 flop x max clock
-    tc_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    # the encoder launches are timed alone (0.02-2 ms each): the burst peak is their denominator;
+    # the sustained one (a seconds-long cuBLAS loop) is reported beside it
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    tc_sustained = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    probe = fv.fv_probe_peaks()                               # measured FP32 FMA and ex2 throughput
     KD = K_COMP * D_DIM
     D16 = (D_DIM + 15) // 16 * 16
 
@@ -624,6 +669,14 @@ def main():
                                   "f32_stats": 2.0 * K_COMP * (2 * D_DIM + 1) * N_DESC},
                          "alu", alu_peak, "TFLOP/s", f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                          "fv_fp32.cu")
+    if roof32.get("achieved"):
+        meas = max(probe["ffma_tflops"], probe["ffma2_tflops"])
+        roof32["peak_measured"] = meas
+        roof32["frac_of_measured"] = roof32["achieved"] / meas
+        roof32["peak_measured_basis"] = "fv_probe_peaks: best of scalar and f32x2 FMA chains on every SM"
+    # error of the timed outputs (the last step's vectors) against the oracle, four frames
+    out_h = out.cpu().numpy()
+    err32 = oracle_errors([(out_h[f], frames[f]) for f in (0, 21, 42, 63)], w, mu, var)
 
     # ---- BF16 precision form: descriptors stored as bf16 in HBM ----
     gbf = fv.fv_gmm_load(w, mu, var, fv.FV_PREC_BF16)
@@ -666,21 +719,29 @@ def main():
         prof = kernel_times(step_bf_1 if name == "bf16" else stepf, max(1, args.steps // 4))
         rows_per_launch = N_DESC * frames_per_call
         roof = roofline_of(prof, {k: v * rows_per_launch for k, v in work_bf.items()}, "tensor", tc_peak,
-                           "TFLOP/s", "MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)",
+                           "TFLOP/s", "MEASURED_PEAKS bf16_tflops (cuBLAS bf16 burst, of measured)",
                            "fv_bf16.cu", {k: v * rows_per_launch for k, v in issued_bf.items()},
                            workload="frame" if frames_per_call == 1 else "batch64")
+        if roof.get("achieved"):
+            roof["frac_of_sustained"] = roof["achieved"] / tc_sustained
         vb = world * args.steps * POOL * N_DESC / (msb / 1e3)
+        # the last step's vectors against the oracle: on the identical (bf16-rounded) descriptors and on
+        # the original FP32 descriptors (input quantisation included)
+        ob = outb.cpu().numpy()
+        pick = (0, 31, 63)
+        err = {"same_bf16_input": oracle_errors([(ob[f], synth.to_bf16_grid(frames[f])) for f in pick], w, mu, var),
+               "fp32_input": oracle_errors([(ob[f], frames[f]) for f in pick], w, mu, var)}
         forms[name] = {"value": vb, "unit": "descriptors/s", "frames_per_s": vb / N_DESC,
                        "frame_streams": best,
                        "us_per_frame_by_streams": {str(ns): 1e3 * v[0] / (args.steps * POOL)
                                                    for ns, v in per_streams.items()},
                        "us_per_frame": 1e3 * msb / (args.steps * POOL), "frames_per_call": frames_per_call,
-                       "ms_per_step": msb / args.steps, "gpu_launches": lb, "roofline": roof,
+                       "ms_per_step": msb / args.steps, "gpu_launches": lb, "roofline": roof, "error": err,
                        "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / max(1, v[0])}
                                    for k, v in prof.items()}}
     # ---- batched form: 256 frames, N ~ U{5000..40000}, one graph launch per step ----
-    forms["batched_graph"] = batched_graph_form(args, gbf, w, mu, var, Xb, stream, barrier, dist, world,
-                                                tc_peak, work_bf, issued_bf)
+    forms["batched_graph"] = batched_graph_form(args, gbf, w, mu, var, Xb, frames, stream, barrier, dist, world,
+                                                tc_peak, work_bf, issued_bf, tc_sustained)
 
     # ---- serving form: 64 streams x 30 fps, K=512 (rank 0 only: one GPU) ----
     if rank == 0 and args.serve_seconds > 0:
@@ -741,6 +802,8 @@ def main():
                        "parallelism": f"dp{world} (frames)"},
             "roofline": roof32, "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / max(1, v[0])}
                                             for k, v in prof32.items()},
+            "error": err32, "tolerance": {"fp32": 1e-4, "bf16": 2e-3},
+            "measured_unit_peaks": probe,
             "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "forms": forms,
         }
         print(json.dumps(line))

@@ -292,6 +292,14 @@ typedef struct {
 } fv_kernel_stat;
 
 FV_API int fv_prof_enable(int on);
+/* Throughput probes of the SM units the plain FP32 form and the softmax use:
+ * every SM runs long independent chains of scalar FP32 fused multiply-adds,
+ * of packed f32x2 fused multiply-adds and of ex2.approx, each timed with CUDA
+ * events on cuda_stream (best of five launches after a warm-up). Outputs
+ * (each nullable): FP32 TFLOP/s counting a multiply-add as 2 flops for the
+ * scalar and packed forms, and ex2 results per second in G/s. Synchronous.
+ * Errors: FV_ERR_CUDA. */
+FV_API int fv_probe_peaks(double *ffma_tflops, double *ffma2_tflops, double *ex2_gops, void *cuda_stream);
 FV_API int fv_prof_collect(fv_kernel_stat *out, int max, int *n_out);
 FV_API int64_t fv_launch_count(void);
 

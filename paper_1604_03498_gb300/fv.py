@@ -125,6 +125,8 @@ def lib():
             L.fv_prof_enable.restype = I
             L.fv_prof_collect.argtypes = [P, I, ctypes.POINTER(I)]
             L.fv_prof_collect.restype = I
+            L.fv_probe_peaks.argtypes = [P, P, P, P]
+            L.fv_probe_peaks.restype = I
             L.fv_launch_count.argtypes = []
             L.fv_launch_count.restype = I64
             _lib = L
@@ -390,6 +392,14 @@ def fv_prof_collect() -> dict:
     n = ctypes.c_int()
     _check(lib().fv_prof_collect(ctypes.cast(arr, ctypes.c_void_p), 64, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def fv_probe_peaks(stream=None) -> dict:
+    """C fv_probe_peaks: measured FP32 FMA (scalar, packed f32x2) TFLOP/s and
+    ex2 G/s of the current device."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().fv_probe_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream(stream)))
+    return {"ffma_tflops": a.value, "ffma2_tflops": b.value, "ex2_gops": c.value}
 
 
 def fv_launch_count() -> int:

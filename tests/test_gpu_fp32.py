@@ -25,6 +25,8 @@ P = fv.FV_PREC_FP32
     (7, 5, 70, 4),
     (256, 80, 777, 5),
     (33, 130, 200, 6),      # D spans three statistics dimension chunks
+    (512, 64, 2000, 7),     # Kp=512: the largest row block (64 x 512 log-likelihoods in shared memory)
+    (500, 37, 1111, 8),     # K padded to 512, D not a multiple of 16, ragged tail
 ])
 def test_fp32_matches_oracle(K, D, N, seed):
     X, w, mu, var = case(K, D, N, seed)
@@ -35,6 +37,19 @@ def test_fp32_matches_oracle(K, D, N, seed):
 
 def test_fp32_full_frame_320x240():
     X, w, mu, var = case(256, 64, 19200, 11)
+    st, out = gpu_encode(P, X, w, mu, var)
+    assert st == fv.FV_OK
+    err = max_err(out, oracle_fv(X, w, mu, var))
+    assert err <= TOL[P], err
+    assert abs(np.linalg.norm(out.astype(np.float64)) - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("K,D,N,seed", [
+    (512, 80, 19200, 17),   # the precision-form comparison shape (320x240 frame, D=80, K=512)
+    (512, 64, 40000, 18),   # the largest serving frame (K=512 GMM, N=40000)
+])
+def test_fp32_full_size_k512(K, D, N, seed):
+    X, w, mu, var = case(K, D, N, seed)
     st, out = gpu_encode(P, X, w, mu, var)
     assert st == fv.FV_OK
     err = max_err(out, oracle_fv(X, w, mu, var))
