@@ -142,3 +142,22 @@ def test_bf16_repeated_calls_are_bitwise_identical(K, D):
     got = ref.cpu().numpy()
     for f in (0, F - 1):
         assert max_err(got[f], oracle_fv(_rounded(frames[f]), w, mu, var)) <= TOL[P]
+
+
+@pytest.mark.parametrize("K,D,N,seed", [(256, 64, 19200, 11), (512, 64, 8000, 13), (512, 64, 11173, 14)])
+def test_bf16_kernel_follows_the_cpu_model_of_its_roundings(K, D, N, seed):
+    """The fused kernel's output follows the CPU model of the precision
+    form's roundings (tests/bf16_emulation.py: bf16 split operands, bf16
+    posteriors), so the error budget measured on the CPU
+    (tests/test_bf16_error_budget.py) is the kernel's: the two agree to well
+    within the tolerance, and both are inside it."""
+    import bf16_emulation as E
+    X, w, mu, var = case(K, D, N, seed)
+    Xr = _rounded(X).astype(np.float64)
+    st, out = gpu_encode(P, X, w, mu, var)
+    assert st == fv.FV_OK
+    model = E.encode(Xr, w, mu, var)
+    ref = oracle_fv(Xr, w, mu, var)
+    assert max_err(out, model) <= TOL[P] / 4
+    assert max_err(out, ref) <= TOL[P]
+    assert max_err(model, ref) <= TOL[P]
