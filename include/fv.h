@@ -147,6 +147,36 @@ FV_API int fv_encode_batch(const fv_gmm *gmm, const float *X_packed, const int64
 FV_API int fv_encode_batch_bf16(const fv_gmm *gmm, const uint16_t *X_bf16, int64_t ld_x,
                          const int64_t *offsets, int B, float *fv_out, void *cuda_stream);
 
+/* Options of fv_encode_batch_opts.
+ *   posterior_threshold  tau in [0, 1). 0 (the default of every other entry
+ *            point) is the exact encoding. tau > 0 is the paper's early
+ *            termination (Sec. 3.3, Algorithm 5, with 1e-6 in the paper):
+ *            statistics terms whose posterior gamma_ik is not above tau are
+ *            dropped (the threshold test of Algorithm 1's second loop), and
+ *            blocks of work whose posteriors are all at or below tau are
+ *            skipped: in the FP32 form a warp's row of 16 components, in the
+ *            BF16 form a 16-row x 128-component K step of the statistics
+ *            GEMM. The result is the thresholded Fisher vector.
+ *   skip_counts  NULL, or DEVICE memory of two uint64 counters to which the
+ *            call adds (skipped blocks, visited blocks) when tau > 0 (the
+ *            caller zeroes them). */
+typedef struct {
+    float posterior_threshold;
+    void *skip_counts;
+} fv_encode_options;
+
+/* fv_encode_batch / fv_encode_batch_bf16 with options (opts may be NULL).
+ *   X          N x D row-major float32 (x_is_bf16 = 0; host or device per
+ *              x_on_device, ld_x ignored) or bfloat16 bit patterns with row
+ *              pitch ld_x (x_is_bf16 = 1; device only, FV_PREC_BF16 handle,
+ *              ld_x >= D and a multiple of 8, 16-byte aligned),
+ *   offsets    B+1 host int64 as in fv_encode_batch.
+ * Errors as fv_encode_batch, and FV_ERR_INVALID for a threshold outside
+ * [0, 1) or skip_counts not in device memory. */
+FV_API int fv_encode_batch_opts(const fv_gmm *gmm, const void *X, int x_is_bf16, int64_t ld_x, const int64_t *offsets,
+                                int B, int x_on_device, float *fv_out, int out_on_device, const fv_encode_options *opts,
+                                void *cuda_stream);
+
 /* ---- batched form: one CUDA-graph launch per batch ---------------------------
  * A plan owns every device buffer a batch of up to max_frames frames and
  * max_rows descriptors needs (bfloat16 input rows, posteriors, statistics

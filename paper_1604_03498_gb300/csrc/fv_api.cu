@@ -224,7 +224,8 @@ struct Scratch {
 };
 
 int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const int64_t *offsets, int B,
-                int x_on_device, float *fv_out, int out_on_device, cudaStream_t st) {
+                int x_on_device, float *fv_out, int out_on_device, cudaStream_t st, float tau = 0.f,
+                unsigned long long *skip_count = nullptr) {
     const int K = g->K, D = g->D, Kp = g->Kp;
     const size_t fvlen = (size_t)2 * K * D;
     int cur = 0;
@@ -315,7 +316,8 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
                 rc = cuda_fail(e, "f32 posteriors launch");
                 break;
             }
-            if ((e = launch_f32_stats(g, (const float *)Xd, gam, und, nslots, part, P, st, true)) != cudaSuccess) {
+            if ((e = launch_f32_stats(g, (const float *)Xd, gam, und, nslots, part, P, st, true, tau, skip_count)) !=
+                cudaSuccess) {
                 rc = cuda_fail(e, "f32 statistics launch");
                 break;
             }
@@ -329,7 +331,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
                 }
                 xb = xconv;
             }
-            rc = run_bf16_encoder(g, xb, ldx_dev, rows, und, ctad, nctas, part, P, errd, st);
+            rc = run_bf16_encoder(g, xb, ldx_dev, rows, und, ctad, nctas, part, P, errd, st, tau, skip_count);
             if (rc != FV_OK) break;
         }
         int max_slots = 1;
@@ -402,6 +404,28 @@ extern "C" int fv_encode_batch_bf16(const fv_gmm *gmm, const uint16_t *X_bf16, i
     if (ld_x < gmm->D || ld_x % 8 != 0) return fail(FV_ERR_INVALID, "ld_x must be >= D and a multiple of 8");
     if (((uintptr_t)X_bf16) % 16 != 0) return fail(FV_ERR_INVALID, "X_bf16 must be 16-byte aligned");
     return encode_impl(gmm, X_bf16, true, ld_x, offsets, B, 1, fv_out, 1, (cudaStream_t)cuda_stream);
+}
+
+extern "C" int fv_encode_batch_opts(const fv_gmm *gmm, const void *X, int x_is_bf16, int64_t ld_x,
+                                    const int64_t *offsets, int B, int x_on_device, float *fv_out, int out_on_device,
+                                    const fv_encode_options *opts, void *cuda_stream) {
+    int rc = check_common(gmm, fv_out);
+    if (rc != FV_OK) return rc;
+    if (B <= 0 || !offsets) return fail(FV_ERR_INVALID, "B must be > 0 and offsets non-NULL");
+    const float tau = opts ? opts->posterior_threshold : 0.f;
+    if (!(tau >= 0.f) || !(tau < 1.f)) return fail(FV_ERR_INVALID, "posterior_threshold must be in [0, 1)");
+    unsigned long long *cnt = opts ? (unsigned long long *)opts->skip_counts : nullptr;
+    if (cnt && !is_device_ptr(cnt)) return fail(FV_ERR_INVALID, "skip_counts must be device memory");
+    if (x_is_bf16) {
+        if (gmm->prec != FV_PREC_BF16) return fail(FV_ERR_INVALID, "bfloat16 descriptors need an FV_PREC_BF16 GMM");
+        if (!x_on_device || !out_on_device)
+            return fail(FV_ERR_INVALID, "bfloat16 descriptors and their output must be device memory");
+        if (ld_x < gmm->D || ld_x % 8 != 0) return fail(FV_ERR_INVALID, "ld_x must be >= D and a multiple of 8");
+        if (((uintptr_t)X) % 16 != 0) return fail(FV_ERR_INVALID, "X must be 16-byte aligned");
+        return encode_impl(gmm, X, true, ld_x, offsets, B, 1, fv_out, 1, (cudaStream_t)cuda_stream, tau, cnt);
+    }
+    return encode_impl(gmm, X, false, 0, offsets, B, x_on_device, fv_out, out_on_device, (cudaStream_t)cuda_stream,
+                       tau, cnt);
 }
 
 // ---- instrumentation ------------------------------------------------------------

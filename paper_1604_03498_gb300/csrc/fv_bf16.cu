@@ -26,6 +26,14 @@
 //    per-block copies of the statistics).
 // The finalise kernel centres the raw moments, scales and normalises.
 //
+// Early termination (Sec. 3.3, Algorithm 5), as block sparsity of the
+// statistics GEMM: with a posterior threshold tau > 0 the softmax writes
+// posteriors not above tau as zeros and marks each 16-row K step of the
+// gamma^T tile that still holds a non-zero posterior; the statistics issuer
+// skips the MMAs of unmarked K steps (a 16-row x 128-component block of
+// posteriors all at or below tau), which add nothing. tau = 0 is the exact
+// encoding and issues every MMA.
+//
 // TMEM (512 columns): two log-likelihood buffers of 128 columns (the next
 // tile's GEMM overlaps this tile's softmax) and the statistics accumulator.
 // Shared memory: the GMM operand [Q_hi | Q_lo | R_hi | R_lo] for the CTA's
@@ -107,11 +115,13 @@ struct EncArgs {
     const int2 *cl_units;     // per cluster: (first unit, number of units)
     float *part;              // [slot][P][Kp] statistics slots
     uint32_t *err;
+    float tau;                // posterior threshold (0: exact, every MMA issued)
+    unsigned long long *skip_count;   // [skipped, issued + skipped] statistics K steps (nullable)
 };
 
 struct EncSmem {
     // byte offsets from the (1024-aligned) dynamic shared-memory base
-    uint32_t b, xr, y, y_stage, g, hx, xchg, cl, bars, misc, total;
+    uint32_t b, xr, y, y_stage, g, hx, xchg, cl, bars, misc, flags, total;
 };
 
 __host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage) {
@@ -135,6 +145,8 @@ __host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage) {
     s.bars = off;
     off += 32u * 8u;
     s.misc = off;
+    off += 16u;
+    s.flags = off;                               // [2 halves][8 K steps] non-zero posterior marks
     off += 16u;
     s.total = off;
     return s;
@@ -386,7 +398,10 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         // ---------------- statistics GEMMs ----------------
         const uint32_t idesc_s = idesc_bf16(kComps, p.ny, true, true);
         const uint32_t sG = smem_u32(smem + L.g);
-        bool issued = false;
+        const volatile uint8_t *flags = smem + L.flags;
+        const bool sparse = p.tau > 0.f;
+        bool issued = false, started = false;
+        unsigned long long nskip = 0, nsteps = 0;
         int i = 0;
         for (TileWalk w(p.units, cu); w.more(); w.next(), ++i) {
             if (w.first() && w.ui > 0) {   // the previous unit's accumulator has been written out
@@ -394,14 +409,26 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             }
             if (!mbar_wait(&bars[EB_GFULL], i & 1, abort_flag, p.err)) break;
             tc_fence_after();
+            if (w.first()) started = false;   // the next MMA initialises the unit's accumulator
             const uint32_t sy = smem_u32(smem + L.y + (i % p.nstage) * L.y_stage);
             for (int q = 0; q < kRows / 16; ++q) {
+                // a K step whose 16 x 128 posteriors are all zero adds nothing;
+                // a unit's last tile issues its first step regardless when
+                // nothing was issued yet (zero posteriors then zero the accumulator)
+                if (sparse) {
+                    ++nsteps;
+                    if (!(flags[q] | flags[8 + q]) && (started || !w.last() || q > 0)) {
+                        ++nskip;
+                        continue;
+                    }
+                }
                 // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
                 // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
                 // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
                 const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
                 const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
-                mma_bf16(tmem + kStatCol, a, b, idesc_s, (w.first() && q == 0) ? 0u : 1u);
+                mma_bf16(tmem + kStatCol, a, b, idesc_s, started ? 1u : 0u);
+                started = true;
             }
             mma_commit(&bars[EB_GFREE]);
             mma_commit(&bars[EB_STFREE + (i & 1)]);
@@ -411,6 +438,10 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         if (issued) {
             mma_commit(&bars[EB_DRAIN2]);
             mbar_drain(&bars[EB_DRAIN2], 0, 2000000000ll);
+        }
+        if (sparse && p.skip_count) {
+            atomicAdd(&p.skip_count[0], nskip);
+            atomicAdd(&p.skip_count[1], nsteps);
         }
     } else if (warp == 2 || warp == 3 || warp >= 12) {
         // ---------------- Y builders: the tile's Y planes from the landing buffer ----------------
@@ -582,11 +613,21 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             // pass B: normalised posteriors -> bf16 gamma^T (second chunk's load in flight)
             tmem_ld32_issue(ta, ra);
             tmem_ld_wait(ra);
+            const float tau = p.tau;
+            bool row_nz = false;   // early termination: a posterior of this row and half above tau
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 uint32_t(&cur)[32] = c ? rb : ra;
                 if (c == 0) tmem_ld32_issue(ta + 32, rb);
                 const float sc = ex2_approx(mc[c] - Mref) * inv;
+                if (tau > 0.f) {   // posteriors not above tau are dropped
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const float g = __uint_as_float(cur[k]) * sc;
+                        row_nz |= g > tau;
+                        cur[k] = g > tau ? cur[k] : 0u;
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {   // 16-byte chunk c * 4 + k of the 128-byte row
                     uint4 v;
@@ -597,6 +638,13 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                     *reinterpret_cast<uint4 *>(gsm + (((c * 4 + k) ^ sw) << 4)) = v;
                 }
                 if (c == 0) tmem_ld_wait(rb);
+            }
+            if (tau > 0.f) {   // marks of this warp's two 16-row K steps (its half of the components)
+                const uint32_t bal = __ballot_sync(0xffffffffu, row_nz);
+                if (lane == 0) {
+                    smem[L.flags + h * 8 + 2 * q] = (bal & 0xFFFFu) != 0u;
+                    smem[L.flags + h * 8 + 2 * q + 1] = (bal >> 16) != 0u;
+                }
             }
             fence_proxy_async_smem();
             tc_fence_before();
@@ -757,7 +805,8 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
 }
 
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, const StatUnit *units,
-                     const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st) {
+                     const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st,
+                     float tau, unsigned long long *skip_count) {
     if (rows <= 0 || n_shares <= 0) return FV_OK;
     if (get_encoder() != cudaSuccess) return fail(FV_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
     EncCfg c;
@@ -782,6 +831,8 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     a.cl_units = cl_units;
     a.part = part;
     a.err = err;
+    a.tau = tau;
+    a.skip_count = skip_count;
     cudaError_t e = cudaFuncSetAttribute(bf16_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return cuda_fail(e, "bf16 encoder: smem attribute");
     cudaLaunchConfig_t cfg;

@@ -20,7 +20,11 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
 // unit, count) of share c, which one cluster of the kernel walks.
 // part: [slot][P][Kp] statistics slots, P = 3*D16 + 1.
 // err: device word a kernel sets when a bounded wait gives up (zeroed by the caller).
+// tau > 0: early termination (posteriors <= tau dropped, all-zero 16-row
+// K steps of the statistics GEMM skipped); skip_count (device, nullable):
+// [skipped, visited] K steps.
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, const StatUnit *units,
-                     const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st);
+                     const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st,
+                     float tau = 0.f, unsigned long long *skip_count = nullptr);
 
 }  // namespace fv

@@ -25,6 +25,14 @@
 // bitwise those of the dense loop. Every block writes its own statistics slot;
 // the finalise kernel reduces the slots in a fixed order, so no atomics touch
 // the result.
+//
+// Early termination (Sec. 3.3, Algorithm 5): with a posterior threshold
+// tau > 0 a term whose posterior is not above tau is dropped (the threshold
+// test of Algorithm 1's second loop), and a warp skips a row when all 16 of
+// its components' posteriors are at or below tau (the paper skips an
+// iteration when all 8 posteriors of its 2 x 4 tile are below 1e-6). The
+// result is the thresholded encoding, not the exact one; tau = 0 runs the
+// exact kernel unchanged.
 #include "fv_internal.h"
 
 namespace fv {
@@ -242,11 +250,14 @@ constexpr int S_BLOCKS_PER_SM = 3;
 // grid.z = 64-dimension chunks. Stages of 32 rows are double-buffered in
 // shared memory and filled by cp.async (16-byte copies when the rows allow,
 // VEC) while the previous stage is consumed.
-template <bool VEC>
+// THRESH: posteriors <= tau are dropped and rows whose 16 posteriors are all
+// <= tau skipped (early termination); skip_count (nullable) receives, per
+// block, the number of (row, 16-component group) pairs skipped and visited.
+template <bool VEC, bool THRESH>
 __global__ void __launch_bounds__(S_THREADS, S_BLOCKS_PER_SM)
 f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ gamma, int Kp, int Dp,
                  const float *__restrict__ mu_kd, const StatUnit *__restrict__ units, float *__restrict__ part,
-                 int P) {
+                 int P, float tau, unsigned long long *__restrict__ skip_count) {
     __shared__ __align__(16) float sG[2][S_RS * S_KC];
     __shared__ __align__(16) float sXs[2][S_RS * S_DC];
 
@@ -309,6 +320,7 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     }
 
     int buf = 0;
+    unsigned skipped = 0, visited = 0;   // (row, 16-component group) pairs of this warp
     for (int r0 = 0; r0 < u.nrows; r0 += S_RS) {
         if (r0 + S_RS < u.nrows) issue(r0 + S_RS, buf ^ 1);
         else cp_async_commit();   // an empty group keeps the wait count uniform
@@ -323,15 +335,25 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
             float4 xb = *reinterpret_cast<const float4 *>(&Xs[dl + 4]);
 #pragma unroll 4
             for (int r = 0; r < S_RS; ++r) {
-                const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+                float gv[4] = {g4.x, g4.y, g4.z, g4.w};
                 const uint64_t xv[4] = {pk2(xa.x, xa.y), pk2(xa.z, xa.w), pk2(xb.x, xb.y), pk2(xb.z, xb.w)};
                 if (r + 1 < S_RS) {
                     g4 = *reinterpret_cast<const float4 *>(&G[(r + 1) * S_KC + cg * S_CPT]);
                     xa = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl]);
                     xb = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl + 4]);
                 }
+                if constexpr (THRESH) {
+#pragma unroll
+                    for (int c = 0; c < S_CPT; ++c) gv[c] = gv[c] > tau ? gv[c] : 0.f;   // dropped terms
+                    if (r0 + r < u.nrows) ++visited;
+                }
                 const bool nz = (gv[0] != 0.f) | (gv[1] != 0.f) | (gv[2] != 0.f) | (gv[3] != 0.f);
-                if (!__any_sync(0xffffffffu, nz)) continue;   // exact zeros for all 16 components
+                if (!__any_sync(0xffffffffu, nz)) {   // exact zeros (or dropped terms) for all 16 components
+                    if constexpr (THRESH) {
+                        if (r0 + r < u.nrows) ++skipped;
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int c = 0; c < S_CPT; ++c) {
                     S0[c] += gv[c];
@@ -348,6 +370,12 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
         }
         __syncthreads();   // the buffer is consumed before it is refilled
         buf ^= 1;
+    }
+    if constexpr (THRESH) {
+        if (skip_count && (threadIdx.x & 31) == 0 && dc0 == 0) {   // one count per warp and component group
+            atomicAdd(&skip_count[0], (unsigned long long)skipped);
+            atomicAdd(&skip_count[1], (unsigned long long)visited);
+        }
     }
     if (!active) return;
     // slot layout part[slot][j][Kp]: this thread's 4 components are contiguous
@@ -404,15 +432,19 @@ cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows,
 }
 
 cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
-                             int n_units, float *part, int P, cudaStream_t st, bool pdl) {
+                             int n_units, float *part, int P, cudaStream_t st, bool pdl, float tau,
+                             unsigned long long *skip_count) {
     if (n_units <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_units, (unsigned)(g->Kp / S_KC), (unsigned)((g->D + S_DC - 1) / S_DC));
     // 16-byte copies need 16-byte aligned rows of X (gamma rows always are)
     const bool vec = (g->D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const bool thr = tau > 0.f;
+    auto kern = vec ? (thr ? f32_stats_kernel<true, true> : f32_stats_kernel<true, false>)
+                    : (thr ? f32_stats_kernel<false, true> : f32_stats_kernel<false, false>);
     {
         KernelTimer kt_("f32_stats", st);
-        return launch_pdl(pdl, vec ? f32_stats_kernel<true> : f32_stats_kernel<false>, grid, dim3(S_THREADS), 0, st, X,
-                          g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units, part, P);
+        return launch_pdl(pdl, kern, grid, dim3(S_THREADS), 0, st, X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units,
+                          part, P, tau, skip_count);
     }
     return cudaGetLastError();
 }

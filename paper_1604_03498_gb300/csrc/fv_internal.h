@@ -138,8 +138,11 @@ cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block
 
 cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma,
                                   cudaStream_t st);
+// tau > 0: early termination (terms with posterior <= tau dropped, all-small
+// rows skipped); skip_count (device, nullable): [skipped, visited] counters.
 cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
-                             int n_units, float *part, int P, cudaStream_t st, bool pdl = false);
+                             int n_units, float *part, int P, cudaStream_t st, bool pdl = false, float tau = 0.f,
+                             unsigned long long *skip_count = nullptr);
 
 // Statistics slots are component-fastest: part[slot][j][Kp], j < P.
 // Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,

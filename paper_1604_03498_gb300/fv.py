@@ -48,6 +48,10 @@ class fv_gmm_desc(ctypes.Structure):
                 ("means", ctypes.c_void_p), ("variances", ctypes.c_void_p)]
 
 
+class fv_encode_options(ctypes.Structure):
+    _fields_ = [("posterior_threshold", ctypes.c_float), ("skip_counts", ctypes.c_void_p)]
+
+
 class fv_batch_plan_config(ctypes.Structure):
     _fields_ = [("max_frames", ctypes.c_int), ("max_rows", ctypes.c_int64), ("autotune", ctypes.c_int),
                 ("tune_cache", ctypes.c_char_p)]
@@ -91,6 +95,8 @@ def lib():
             L.fv_encode.restype = I
             L.fv_encode_batch.argtypes = [P, P, P, I, I, P, I, P]
             L.fv_encode_batch.restype = I
+            L.fv_encode_batch_opts.argtypes = [P, P, I, I64, P, I, I, P, I, ctypes.POINTER(fv_encode_options), P]
+            L.fv_encode_batch_opts.restype = I
             L.fv_encode_batch_bf16.argtypes = [P, P, I64, P, I, P, P]
             L.fv_encode_batch_bf16.restype = I
             L.fv_last_error.argtypes = []
@@ -258,6 +264,25 @@ def fv_encode_batch_bf16(g: Gmm, X_bf16, ld_x: int, offsets, out, stream=None,
     op, _ = _ptr(out)
     return _check(lib().fv_encode_batch_bf16(g.handle, xp, int(ld_x), offs.ctypes.data, B, op, _stream(stream)),
                   allow)
+
+
+def fv_encode_batch_opts(g: Gmm, X, offsets, out, tau: float = 0.0, skip_counts=None, ld_x: int = 0,
+                         stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    """C fv_encode_batch_opts: X is float32 (host or CUDA) or a CUDA bfloat16
+    tensor (row pitch ld_x, default D); tau the posterior threshold (early
+    termination); skip_counts an optional CUDA int64 tensor of 2 counters."""
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    xp, xd = _ptr(X)
+    op, od = _ptr(out)
+    is_bf16 = 0
+    try:
+        import torch
+        is_bf16 = int(isinstance(X, torch.Tensor) and X.dtype == torch.bfloat16)
+    except ImportError:
+        pass
+    opt = fv_encode_options(float(tau), _ptr(skip_counts)[0] if skip_counts is not None else None)
+    return _check(lib().fv_encode_batch_opts(g.handle, xp, is_bf16, int(ld_x or g.D), offs.ctypes.data, offs.size - 1,
+                                             xd, op, od, ctypes.byref(opt), _stream(stream)), allow)
 
 
 def fv_encode_noalloc(g: Gmm, X, out, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
