@@ -51,6 +51,8 @@ def _bind(lib):
     lib.fvo_log_likelihoods.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
     lib.fvo_posteriors.restype = ctypes.c_int
     lib.fvo_posteriors.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
+    lib.fvo_em_step.restype = ctypes.c_int
+    lib.fvo_em_step.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P, P, ctypes.c_double, P, P, P, P]
     return lib
 
 
@@ -150,3 +152,21 @@ def posteriors(X, w, mu, var):
     st = lib.fvo_posteriors(N, K, _p(np.ascontiguousarray(L if N else np.zeros((1, K)))), _p(g), _p(lse))
     assert st == 0, st
     return g[:N], lse[:N]
+
+
+def em_step(X, w, mu, var, reg: float = 0.0):
+    """One EM step of the diagonal GMM from its definitions (FP64): returns
+    (w', mu', var', mean log-likelihood of X under the input model)."""
+    lib = _load()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    var = np.ascontiguousarray(var, dtype=np.float64)
+    K, D = mu.shape
+    N = X.shape[0]
+    w2, mu2, var2 = np.zeros(K), np.zeros((K, D)), np.zeros((K, D))
+    ll = ctypes.c_double()
+    st = lib.fvo_em_step(N, D, K, _p(X), _p(w), _p(mu), _p(var), float(reg), _p(w2), _p(mu2), _p(var2),
+                         ctypes.byref(ll))
+    assert st == 0, st
+    return w2, mu2, var2, ll.value

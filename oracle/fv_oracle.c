@@ -204,3 +204,59 @@ int fvo_encode(int64_t N, int D, int K,
     free(S0);
     return rc;
 }
+
+/* One expectation-maximisation step for the diagonal GMM (the model the
+ * paper's encoder assumes trained beforehand, Sec. 3.1), from the
+ * definitions: with the posteriors gamma of the input model,
+ *   N_k        = sum_i gamma_ik + 10 eps      (eps = 2^-52, keeps an empty
+ *                                              component's divisions finite)
+ *   w'_k       = N_k / N
+ *   mu'_kd     = sum_i gamma_ik x_id / N_k
+ *   sigma2'_kd = sum_i gamma_ik (x_id - mu'_kd)^2 / N_k + reg
+ * and the mean log-likelihood of the descriptors under the INPUT model,
+ *   mean_loglik = 1/N sum_i log sum_k w_k N(x_i; mu_k, sigma2_k).
+ * Outputs: w_out (K), mu_out, var_out (K x D), mean_loglik (nullable). */
+int fvo_em_step(int64_t N, int D, int K, const double *X, const double *w, const double *mu, const double *var,
+                double reg, double *w_out, double *mu_out, double *var_out, double *mean_loglik) {
+    if (N <= 0 || D <= 0 || K <= 0 || !X || !w || !mu || !var || !w_out || !mu_out || !var_out) return FVO_BADARG;
+    double *L = (double *)malloc(sizeof(double) * (size_t)(N * K));
+    double *gam = (double *)malloc(sizeof(double) * (size_t)(N * K));
+    double *lse = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!L || !gam || !lse) {
+        free(L);
+        free(gam);
+        free(lse);
+        return FVO_NOMEM;
+    }
+    int rc = fvo_log_likelihoods(N, D, K, X, w, mu, var, L);
+    if (rc == FVO_OK) rc = fvo_posteriors(N, K, L, gam, lse);
+    if (rc == FVO_OK) {
+        const double two_pi_term = 0.5 * D * log(2.0 * 3.14159265358979323846);
+        if (mean_loglik) {
+            double s = 0.0;
+            for (int64_t i = 0; i < N; ++i) s += lse[i] - two_pi_term;
+            *mean_loglik = s / (double)N;
+        }
+        for (int k = 0; k < K; ++k) {
+            double nk = 10.0 * 2.220446049250313e-16;
+            for (int64_t i = 0; i < N; ++i) nk += gam[i * K + k];
+            w_out[k] = nk / (double)N;
+            for (int d = 0; d < D; ++d) {
+                double s1 = 0.0;
+                for (int64_t i = 0; i < N; ++i) s1 += gam[i * K + k] * X[i * D + d];
+                const double m = s1 / nk;
+                double s2 = 0.0;
+                for (int64_t i = 0; i < N; ++i) {
+                    const double r = X[i * D + d] - m;
+                    s2 += gam[i * K + k] * r * r;
+                }
+                mu_out[(int64_t)k * D + d] = m;
+                var_out[(int64_t)k * D + d] = s2 / nk + reg;
+            }
+        }
+    }
+    free(L);
+    free(gam);
+    free(lse);
+    return rc;
+}
