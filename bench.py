@@ -328,6 +328,44 @@ def early_termination_form(args, g32, w, mu, var, frames, Xd, out, stream, fork_
             "oracle_threshold_vs_exact": max(float(np.abs(t - e).max()) for t, e in zip(thr, exact))}
 
 
+def em_form(args, w, mu, var, frames, Xd, stream, barrier, dist, world):
+    """GMM training (EM) on the GPU: one fv_gmm_em_step (E-step = the FP32
+    form's posteriors and statistics; closed-form M-step) per 320x240-shaped
+    frame of the pool, device outputs; checked against the oracle's EM step
+    on one frame."""
+    import torch
+    from paper_1604_03498_gb300 import fv
+    import oracle
+    K, D = mu.shape
+    g = fv.fv_gmm_load(w, mu + 0.25, var, fv.FV_PREC_FP32)
+    wo = torch.zeros(K, device="cuda")
+    muo = torch.zeros(K, D, device="cuda")
+    varo = torch.zeros(K, D, device="cuda")
+    L = fv.lib()
+    F = min(16, len(frames))
+
+    def step():
+        for f in range(F):
+            L.fv_gmm_em_step(g.handle, Xd[f].data_ptr(), N_DESC, 1, 1e-6, wo.data_ptr(), muo.data_ptr(),
+                             varo.data_ptr(), 1, None, stream.cuda_stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 20))
+    ms, launches = timed(step, steps, stream, barrier, dist)
+    got = fv.fv_gmm_em_step(g, frames[0], reg_covar=1e-6)
+    ref = oracle.em_step(frames[0], w, mu + 0.25, var, reg=1e-6)
+    g.close()
+    return {"value": world * steps * F * N_DESC / (ms / 1e3), "unit": "descriptors/s (one EM step)",
+            "us_per_step_per_frame": 1e3 * ms / (steps * F), "gpu_launches": launches,
+            "workload": f"EM step of a K={K}, D={D} GMM on one 320x240-shaped frame (N={N_DESC})",
+            "max_rel_err_weights": float(np.max(np.abs(got[0] - ref[0]) / ref[0])),
+            "max_err_means_in_sigma": float(np.max(np.abs(got[1] - ref[1]) / np.sqrt(ref[2]))),
+            "max_rel_err_variances": float(np.max(np.abs(got[2] - ref[2]) / ref[2])),
+            "loglik_gpu": got[3], "loglik_oracle": ref[3]}
+
+
 def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, pool_f32, stream, barrier, dist, world, tc_peak, work_bf,
                        issued_bf, tc_sustained):
     """256 frames with N ~ Uniform{5000..40000} (D=64, K=256, bf16 descriptors
@@ -727,6 +765,9 @@ def main():
     forms = {}
     forms["fp32_early_termination"] = early_termination_form(args, g32, w, mu, var, frames, Xd, out, stream,
                                                              fork_join, fstreams, nfs, barrier, dist, world, ms)
+
+    # ---- GMM training by EM on the same frames ----
+    forms["gmm_em"] = em_form(args, w, mu, var, frames, Xd, stream, barrier, dist, world)
 
     # ---- BF16 precision form: descriptors stored as bf16 in HBM ----
     gbf = fv.fv_gmm_load(w, mu, var, fv.FV_PREC_BF16)

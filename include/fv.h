@@ -177,6 +177,41 @@ FV_API int fv_encode_batch_opts(const fv_gmm *gmm, const void *X, int x_is_bf16,
                                 int B, int x_on_device, float *fv_out, int out_on_device, const fv_encode_options *opts,
                                 void *cuda_stream);
 
+/* ---- GMM training: expectation-maximisation on the GPU -----------------------
+ * The paper encodes with a GMM trained beforehand (Sec. 3.1). These calls
+ * train one on the GPU with the encoder's own kernels: the E-step is the
+ * plain FP32 form's posteriors and centred statistics (Algorithm 1), the
+ * M-step the closed form for a diagonal GMM,
+ *   N_k = sum_i gamma_ik + 10 eps (eps = 2^-52),  w'_k = N_k / N,
+ *   mu'_kd = sum_i gamma_ik x_id / N_k,
+ *   var'_kd = sum_i gamma_ik (x_id - mu'_kd)^2 / N_k + reg_covar,
+ * formed in FP64 from the FP32 sums centred on the current means. */
+
+/* One EM step. gmm: an FV_PREC_FP32 handle (the current model). X: N x D
+ * float32 (host or device per x_on_device). Outputs w_out (K), mu_out and
+ * var_out (K x D row-major), host or device per out_on_device. mean_loglik
+ * (host, nullable) receives 1/N sum_i log p(x_i) under the CURRENT model
+ * (the E-step's value). Synchronous when an output is on the host or
+ * mean_loglik is given. reg_covar >= 0 is added to every new variance.
+ * Errors: FV_ERR_INVALID, FV_ERR_EMPTY (N == 0), FV_ERR_OOM, FV_ERR_CUDA. */
+FV_API int fv_gmm_em_step(const fv_gmm *gmm, const float *X, int64_t N, int x_on_device, double reg_covar,
+                          float *w_out, float *mu_out, float *var_out, int out_on_device, double *mean_loglik,
+                          void *cuda_stream);
+
+/* EM from the initial model `init` (host parameters, checked as by
+ * fv_gmm_load) for at most max_iter steps, stopping early once the mean
+ * log-likelihood changes by less than tol between steps; every step runs on
+ * the device (the GMM preparation kernel re-derives the encoder's operands
+ * from the new parameters between steps). Outputs (host): the final
+ * w_out (K), mu_out and var_out (K x D), n_iter (steps run, nullable) and
+ * mean_loglik (nullable: the last E-step's mean log-likelihood, i.e. under
+ * the model before the last M-step). Synchronous. A variance that collapses
+ * to zero (reg_covar = 0 and a component on a single point) makes the
+ * log-likelihood non-finite: FV_ERR_INVALID. */
+FV_API int fv_gmm_fit(const fv_gmm_desc *init, const float *X, int64_t N, int x_on_device, int max_iter, double tol,
+                      double reg_covar, float *w_out, float *mu_out, float *var_out, int *n_iter, double *mean_loglik,
+                      void *cuda_stream);
+
 /* ---- batched form: one CUDA-graph launch per batch ---------------------------
  * A plan owns every device buffer a batch of up to max_frames frames and
  * max_rows descriptors needs (bfloat16 input rows, posteriors, statistics

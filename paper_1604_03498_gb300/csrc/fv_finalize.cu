@@ -202,6 +202,19 @@ finalize_b_kernel(int K, int D, int nb, const double *__restrict__ sq, float *__
 
 }  // namespace
 
+cudaError_t launch_slot_reduce(const fv_gmm *g, float *part, int P, const FrameInfo *frames, int B, int max_slots,
+                               cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    const bool split = max_slots >= 16;
+    const int J = split ? 1 : 8;
+    {
+        KernelTimer kt_("finalize_r", st);
+        finalize_r_kernel<<<dim3((unsigned)((P + J - 1) / J), (unsigned)(g->Kp / 32), (unsigned)B), 256, 0, st>>>(
+            part, P, g->Kp, split, frames, nullptr);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments, const FrameInfo *frames,
                             int B, double *sq, float *out, cudaStream_t st, const uint32_t *err, const int *B_dev,
                             int max_slots, bool pdl) {

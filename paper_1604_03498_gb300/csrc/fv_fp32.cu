@@ -99,7 +99,7 @@ template <int CPL>
 __global__ void __launch_bounds__(P_THREADS)
 f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
                       const float *__restrict__ s_t, const float *__restrict__ nms_t,
-                      const float *__restrict__ cst, float *__restrict__ gamma) {
+                      const float *__restrict__ cst, float *__restrict__ gamma, float *__restrict__ lse) {
     constexpr int KC = 32 * CPL;
     constexpr int XS = P_BM + 4;
     constexpr int STAGE = 2 * P_DS * KC + P_DS * XS;
@@ -229,6 +229,8 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        // the row's log-sum-exp, log sum_k exp(l_ik) = ln 2 (m + log2 z) (natural log; EM's log-likelihood)
+        if (lse && lane == 0) lse[row] = (m + log2f(z)) * 0.69314718055994531f;
         const float iz = 1.0f / z;
         float *G = gamma + row * Kp;
 #pragma unroll
@@ -403,7 +405,8 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
 
 }  // namespace
 
-cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma, cudaStream_t st) {
+cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma, cudaStream_t st,
+                                  float *lse) {
     if (rows <= 0) return cudaSuccess;
     const int Kp = g->Kp;
     const int cpl = (Kp % 128 == 0) ? 4 : 2;
@@ -417,7 +420,7 @@ cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows,
         {
         KernelTimer kt_("f32_posteriors", st);
         f32_posteriors_kernel<4><<<grid, P_THREADS, smem, st>>>(X, rows, g->D, Kp, g->dev.s_t, g->dev.nms_t,
-                                                                g->dev.cst, gamma);
+                                                                g->dev.cst, gamma, lse);
     }
     } else {
         e = cudaFuncSetAttribute(f32_posteriors_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -425,7 +428,7 @@ cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows,
         {
         KernelTimer kt_("f32_posteriors", st);
         f32_posteriors_kernel<2><<<grid, P_THREADS, smem, st>>>(X, rows, g->D, Kp, g->dev.s_t, g->dev.nms_t,
-                                                                g->dev.cst, gamma);
+                                                                g->dev.cst, gamma, lse);
     }
     }
     return cudaGetLastError();

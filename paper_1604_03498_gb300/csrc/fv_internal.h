@@ -72,6 +72,9 @@ struct GmmDev {
     // the same constants before rounding: [0, Kp) log w - 1/2 sum log sigma^2,
     // [Kp, 2 Kp) minus 1/2 sum mu^2/sigma^2 (FP64; -inf on padding)
     double *c64;
+    // the parameters as loaded (FP32): [K] weights, [K][D] means, [K][D]
+    // variances (the preparation kernel's input)
+    float *params;
 };
 
 }  // namespace fv
@@ -136,8 +139,9 @@ cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// lse (nullable): per-row log sum_k exp(l_ik), natural log (EM log-likelihood).
 cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma,
-                                  cudaStream_t st);
+                                  cudaStream_t st, float *lse = nullptr);
 // tau > 0: early termination (terms with posterior <= tau dropped, all-small
 // rows skipped); skip_count (device, nullable): [skipped, visited] counters.
 cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
@@ -155,6 +159,10 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 // correct; it picks the reduction's split).
 // err (nullable): device error word of the call; when a kernel set it, every
 // output element becomes NaN so a failed encode can never look valid.
+// Only the slot reduction of launch_finalize: every frame's slots summed
+// into its first slot in the canonical order.
+cudaError_t launch_slot_reduce(const fv_gmm *g, float *part, int P, const FrameInfo *frames, int B, int max_slots,
+                               cudaStream_t st);
 cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments,
                             const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
                             const uint32_t *err = nullptr, const int *B_dev = nullptr, int max_slots = 1,

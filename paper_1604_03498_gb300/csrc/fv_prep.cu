@@ -232,6 +232,7 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     d.cfull = precision == FV_PREC_BF16 ? (float *)(base + o_cfull) : nullptr;
     d.cl2 = precision == FV_PREC_BF16 ? (float *)(base + o_cl2) : nullptr;
     float *in = (float *)(base + o_in);
+    d.params = in;
 
     cudaStream_t st;
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {

@@ -125,6 +125,12 @@ def lib():
             L.fv_server_stats.restype = I
             L.fv_server_destroy.argtypes = [P]
             L.fv_server_destroy.restype = None
+            L.fv_gmm_em_step.argtypes = [P, P, I64, I, ctypes.c_double, P, P, P, I, ctypes.POINTER(ctypes.c_double),
+                                         P]
+            L.fv_gmm_em_step.restype = I
+            L.fv_gmm_fit.argtypes = [ctypes.POINTER(fv_gmm_desc), P, I64, I, I, ctypes.c_double, ctypes.c_double, P, P,
+                                     P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double), P]
+            L.fv_gmm_fit.restype = I
             L.fv_encode_noalloc.argtypes = [P, P, I64, P, P]
             L.fv_encode_noalloc.restype = I
             L.fv_prof_enable.argtypes = [I]
@@ -292,6 +298,38 @@ def fv_encode_noalloc(g: Gmm, X, out, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) 
     xp, _ = _ptr(X)
     op, _ = _ptr(out)
     return _check(lib().fv_encode_noalloc(g.handle, xp, int(X.shape[0]), op, _stream(stream)), allow)
+
+
+def fv_gmm_em_step(g: Gmm, X, reg_covar: float = 1e-6, stream=None):
+    """C fv_gmm_em_step with host outputs: returns (w, mu, var, mean_loglik)."""
+    K, D = g.K, g.D
+    xp, xd = _ptr(X)
+    w = np.zeros(K, np.float32)
+    mu = np.zeros((K, D), np.float32)
+    var = np.zeros((K, D), np.float32)
+    ll = ctypes.c_double()
+    _check(lib().fv_gmm_em_step(g.handle, xp, int(X.shape[0]), xd, float(reg_covar), w.ctypes.data, mu.ctypes.data,
+                                var.ctypes.data, 0, ctypes.byref(ll), _stream(stream)))
+    return w, mu, var, ll.value
+
+
+def fv_gmm_fit(w0, mu0, var0, X, max_iter: int = 100, tol: float = 1e-3, reg_covar: float = 1e-6, stream=None):
+    """C fv_gmm_fit: returns (w, mu, var, n_iter, mean_loglik)."""
+    w0 = np.ascontiguousarray(np.asarray(w0, dtype=np.float32))
+    mu0 = np.ascontiguousarray(np.asarray(mu0, dtype=np.float32))
+    var0 = np.ascontiguousarray(np.asarray(var0, dtype=np.float32))
+    K, D = mu0.shape
+    desc = fv_gmm_desc(K, D, w0.ctypes.data, mu0.ctypes.data, var0.ctypes.data)
+    xp, xd = _ptr(X)
+    w = np.zeros(K, np.float32)
+    mu = np.zeros((K, D), np.float32)
+    var = np.zeros((K, D), np.float32)
+    it = ctypes.c_int()
+    ll = ctypes.c_double()
+    _check(lib().fv_gmm_fit(ctypes.byref(desc), xp, int(X.shape[0]), xd, int(max_iter), float(tol), float(reg_covar),
+                            w.ctypes.data, mu.ctypes.data, var.ctypes.data, ctypes.byref(it), ctypes.byref(ll),
+                            _stream(stream)))
+    return w, mu, var, it.value, ll.value
 
 
 class BatchPlan:
