@@ -51,6 +51,8 @@ def _bind(lib):
     lib.fvo_log_likelihoods.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
     lib.fvo_posteriors.restype = ctypes.c_int
     lib.fvo_posteriors.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
+    lib.fvo_pca_project.restype = ctypes.c_int
+    lib.fvo_pca_project.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
     lib.fvo_em_step.restype = ctypes.c_int
     lib.fvo_em_step.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, P, P, P, ctypes.c_double, P, P, P, P]
     return lib
@@ -170,3 +172,20 @@ def em_step(X, w, mu, var, reg: float = 0.0):
                          ctypes.byref(ll))
     assert st == 0, st
     return w2, mu2, var2, ll.value
+
+
+def pca_project(X, basis, mean=None, xy=None):
+    """Sec. 3.1's descriptor step: y_i = [basis (x_i - mean); xy_i] in FP64
+    (basis m x Din, rows the principal directions; xy N x 2 or None)."""
+    lib = _load()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    P = np.ascontiguousarray(basis, dtype=np.float64)
+    m, Din = P.shape
+    N = X.shape[0]
+    mean = None if mean is None else np.ascontiguousarray(mean, dtype=np.float64)
+    xy = None if xy is None else np.ascontiguousarray(xy, dtype=np.float64)
+    D = m + (2 if xy is not None else 0)
+    Y = np.zeros((max(N, 1), D))
+    st = lib.fvo_pca_project(N, Din, m, _p(X if N else np.zeros((1, Din))), _p(mean), _p(P), _p(xy), _p(Y))
+    assert st == 0, st
+    return Y[:N]

@@ -260,3 +260,28 @@ int fvo_em_step(int64_t N, int D, int K, const double *X, const double *w, const
     free(lse);
     return rc;
 }
+
+/* The descriptor step of Sec. 3.1 before the encoding: a 128-dimensional
+ * descriptor x is reduced to m dimensions by PCA and the normalised X and Y
+ * position of the descriptor is appended, D = m + 2:
+ *   y_i = [ P (x_i - mean) ; xy_i ]
+ * P is the m x Din matrix of principal directions (rows), mean the Din-vector
+ * the PCA was centred on, xy_i the two normalised coordinates (omitted when
+ * xy is NULL, D = m). Y is N x D row-major. */
+int fvo_pca_project(int64_t N, int Din, int m, const double *X, const double *mean, const double *P, const double *xy,
+                    double *Y) {
+    if (N < 0 || Din <= 0 || m <= 0 || !X || !P || !Y) return FVO_BADARG;
+    const int D = m + (xy ? 2 : 0);
+    for (int64_t i = 0; i < N; ++i) {
+        for (int j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < Din; ++k) s += P[(int64_t)j * Din + k] * (X[i * Din + k] - (mean ? mean[k] : 0.0));
+            Y[i * D + j] = s;
+        }
+        if (xy) {
+            Y[i * D + m] = xy[2 * i];
+            Y[i * D + m + 1] = xy[2 * i + 1];
+        }
+    }
+    return FVO_OK;
+}

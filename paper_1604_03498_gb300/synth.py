@@ -30,6 +30,9 @@ STREAM_GMM = 1
 STREAM_FRAMES = 2
 STREAM_SIZES = 3
 STREAM_ARRIVALS = 4
+STREAM_SIFT = 5
+STREAM_PCA = 6
+STREAM_IMAGES = 7
 
 
 def _rng(*key: int) -> np.random.Generator:
@@ -102,3 +105,33 @@ def to_bf16_grid(X: np.ndarray) -> np.ndarray:
     lsb = (a >> 16) & 1
     r = ((a + 0x7FFF + lsb) >> 16) << 16
     return (r.astype(np.uint32)).view(np.float32).reshape(X.shape)
+
+
+def sample_sift_like(N: int, Din: int = 128, seed: int = 0) -> np.ndarray:
+    """N raw descriptors shaped like SIFT histograms (float32, N x Din):
+    non-negative gradient-orientation mass with a few dominant bins per
+    descriptor, unit L2 norm, entries capped at 0.2 and renormalised (the
+    normalisation SIFT descriptors carry)."""
+    g = _rng(STREAM_SIFT, seed, N, Din)
+    base = g.gamma(0.6, 1.0, size=(N, Din))
+    x = base / np.maximum(np.linalg.norm(base, axis=1, keepdims=True), 1e-12)
+    x = np.minimum(x, 0.2)
+    x = x / np.maximum(np.linalg.norm(x, axis=1, keepdims=True), 1e-12)
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def make_pca(Din: int = 128, m: int = 62, seed: int = 0):
+    """A synthetic PCA: (basis m x Din with orthonormal rows drawn uniformly,
+    mean Din) as float32. The basis comes from the QR factor of a Gaussian
+    matrix (a random rotation), the mean ~ U(0, 0.15) like SIFT entries."""
+    g = _rng(STREAM_PCA, seed, Din, m)
+    q, r = np.linalg.qr(g.standard_normal((Din, m)))
+    q = q * np.sign(np.diag(r))[None, :]
+    mean = g.uniform(0.0, 0.15, size=Din)
+    return np.ascontiguousarray(q.T, dtype=np.float32), mean.astype(np.float32)
+
+
+def sample_positions(N: int, seed: int = 0) -> np.ndarray:
+    """Normalised (x, y) positions of N descriptors, Uniform(-0.5, 0.5)^2."""
+    g = _rng(STREAM_IMAGES, seed, N)
+    return np.ascontiguousarray(g.uniform(-0.5, 0.5, size=(N, 2)), dtype=np.float32)
