@@ -366,6 +366,69 @@ def em_form(args, w, mu, var, frames, Xd, stream, barrier, dist, world):
             "loglik_gpu": got[3], "loglik_oracle": ref[3]}
 
 
+def pca_form(args, stream, barrier, dist, world, hbm_peak):
+    """Raw 128-d descriptors in, Fisher vectors out (Sec. 3.1): the PCA
+    projection to m = 62 plus the normalised (x, y) position (D = 64) as a
+    prologue kernel, then the encoder (K = 256), one 320x240-shaped frame
+    (19200 SIFT-like descriptors, 9.8 MB of FP32) per fv_encode_pca call, for
+    both precision forms. The projection kernels' own rates are reported
+    beside it (the tcgen05 kernel moves 512 B in and 128 B out per row)."""
+    import torch
+    from paper_1604_03498_gb300 import fv
+    import oracle
+    F, m, K, Din = 16, 62, 256, 128
+    Xs = [synth.sample_sift_like(N_DESC, Din, seed=700 + f) for f in range(F)]
+    xys = [synth.sample_positions(N_DESC, seed=700 + f) for f in range(F)]
+    P, mean = synth.make_pca(Din, m, seed=7)
+    w, mu, var = synth.make_gmm(K, m + 2, seed=7)
+    mu, var = (0.3 * mu).astype(np.float32), (0.05 * var).astype(np.float32)
+    Xd = torch.from_numpy(np.stack(Xs)).cuda()
+    xyd = torch.from_numpy(np.stack(xys)).cuda()
+    pca = fv.fv_pca_load(P, mean)
+    res = {"workload": f"{F} frames x {N_DESC} SIFT-like 128-d descriptors -> PCA m={m} + (x, y) -> D={m + 2}, "
+                       f"K={K}; one frame per fv_encode_pca call"}
+    for tag, prec in (("fp32", fv.FV_PREC_FP32), ("bf16", fv.FV_PREC_BF16)):
+        g = fv.fv_gmm_load(w, mu, var, prec)
+        out = torch.zeros(F, 2 * K * (m + 2), device="cuda")
+
+        def step():
+            for f in range(F):
+                fv.fv_encode_pca(g, pca, Xd[f], xyd[f], [0, N_DESC], out[f:f + 1], stream=stream.cuda_stream,
+                                 allow=(fv.FV_OK,))
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        steps = max(3, min(args.steps, 20))
+        ms, launches = timed(step, steps, stream, barrier, dist)
+        prof = kernel_times(step, 2)
+        kname = "pca_" + tag
+        n, kms = prof.get(kname, (1, float("nan")))
+        per = kms / max(1, n) / 1e3
+        r = {"value": world * steps * F * N_DESC / (ms / 1e3), "unit": "descriptors/s (raw 128-d in)",
+             "us_per_frame": 1e3 * ms / (steps * F), "gpu_launches": launches,
+             "projection_kernel_us": per * 1e6,
+             "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / max(1, v[0])} for k, v in prof.items()}}
+        if tag == "bf16":
+            r["projection_roofline"] = {"bound": "hbm", "achieved": (Din * 4 + 80 * 2) * N_DESC / per / 1e9,
+                                        "peak": hbm_peak, "unit": "GB/s",
+                                        "frac": (Din * 4 + 80 * 2) * N_DESC / per / 1e9 / hbm_peak,
+                                        "bytes": "512 B of FP32 descriptor read + 160 B of bf16 row written per row"}
+        else:
+            r["projection_tflops"] = 2.0 * Din * m * N_DESC / per / 1e12
+        oh = out.cpu().numpy()
+        errs = []
+        for f in (0, F - 1):
+            Y = oracle.pca_project(Xs[f], P, mean, xys[f])
+            Yin = Y if prec == fv.FV_PREC_FP32 else synth.to_bf16_grid(Y.astype(np.float32))
+            errs.append(float(np.abs(oh[f] - oracle.encode(Yin, w, mu, var)["fv"]).max()))
+        r["max_abs_err_vs_oracle"] = max(errs)
+        res[tag] = r
+        g.close()
+    pca.close()
+    return res
+
+
 def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, pool_f32, stream, barrier, dist, world, tc_peak, work_bf,
                        issued_bf, tc_sustained):
     """256 frames with N ~ Uniform{5000..40000} (D=64, K=256, bf16 descriptors
@@ -765,6 +828,9 @@ def main():
     forms = {}
     forms["fp32_early_termination"] = early_termination_form(args, g32, w, mu, var, frames, Xd, out, stream,
                                                              fork_join, fstreams, nfs, barrier, dist, world, ms)
+
+    # ---- raw descriptors through the PCA + position prologue ----
+    forms["pca_encode"] = pca_form(args, stream, barrier, dist, world, float(peaks.get("hbm_gbs", 6800.0)))
 
     # ---- GMM training by EM on the same frames ----
     forms["gmm_em"] = em_form(args, w, mu, var, frames, Xd, stream, barrier, dist, world)

@@ -177,6 +177,47 @@ FV_API int fv_encode_batch_opts(const fv_gmm *gmm, const void *X, int x_is_bf16,
                                 int B, int x_on_device, float *fv_out, int out_on_device, const fv_encode_options *opts,
                                 void *cuda_stream);
 
+/* ---- descriptor step before the encoding: PCA + positions (Sec. 3.1) ---------
+ * The paper reduces each 128-dimensional dense-SIFT descriptor to m
+ * dimensions with PCA and appends the descriptor's normalised X and Y
+ * position, D = m + 2 (D = 82 in Sec. 4):
+ *   y_i = [ P (x_i - mean) ; xy_i ].
+ * The projection runs on the GPU as a prologue of the encoder: an FP32 SIMT
+ * kernel for FV_PREC_FP32 handles, a tcgen05 GEMM for FV_PREC_BF16 handles
+ * (x - mean and P split into bfloat16 hi + lo parts, three products with
+ * FP32 accumulation, the result rounded to the bfloat16 rows the encoder
+ * reads). */
+typedef struct fv_pca fv_pca;
+
+/* Load a projection onto the current device. basis: m x Din row-major host
+ * floats (rows are the principal directions), mean: Din host floats the PCA
+ * was centred on (NULL = zeros). 1 <= m <= 78 (so that D = m + 2 fits the
+ * BF16 form's D <= 80), Din a multiple of 16 in 16..256. Copies its inputs.
+ * Errors: FV_ERR_INVALID (NULL, non-finite), FV_ERR_UNSUPPORTED (sizes),
+ * FV_ERR_OOM, FV_ERR_CUDA. */
+FV_API int fv_pca_load(const float *basis, const float *mean, int m, int Din, fv_pca **out);
+FV_API int fv_pca_info(const fv_pca *pca, int *m, int *Din);
+FV_API void fv_pca_free(fv_pca *pca);
+
+/* Project N descriptors (X: N x Din float32, device, 16-byte aligned; xy:
+ * N x 2 float32 normalised positions, device, or NULL) into Y (device):
+ * float32 rows of pitch m + 2 (m without xy) when y_bf16 = 0, or bfloat16
+ * rows of pitch ld_y (a multiple of 16, >= D, 16-byte aligned; padding
+ * zeroed) with the tcgen05 kernel when y_bf16 = 1. Stream-ordered. Errors:
+ * FV_ERR_INVALID, FV_ERR_EMPTY (N == 0), FV_ERR_CUDA. */
+FV_API int fv_pca_project(const fv_pca *pca, const float *X, const float *xy, int64_t N, void *Y, int y_bf16,
+                          int64_t ld_y, void *cuda_stream);
+
+/* Encode B frames of raw descriptors: the PCA step above, then the encoder
+ * of the GMM's precision on the projected rows (the projected rows never
+ * leave the device). X: offsets[B] x Din float32, xy: offsets[B] x 2 (or
+ * NULL), both on the host or both on the device per x_on_device; the GMM's
+ * D must be m + 2 (m when xy is NULL). offsets and fv_out as in
+ * fv_encode_batch. Errors as fv_encode_batch, and FV_ERR_DEVICE (host
+ * output only) if the projection gave up on a bounded wait. */
+FV_API int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *X, const float *xy, const int64_t *offsets,
+                         int B, int x_on_device, float *fv_out, int out_on_device, void *cuda_stream);
+
 /* ---- GMM training: expectation-maximisation on the GPU -----------------------
  * The paper encodes with a GMM trained beforehand (Sec. 3.1). These calls
  * train one on the GPU with the encoder's own kernels: the E-step is the

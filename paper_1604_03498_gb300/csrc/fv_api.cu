@@ -428,6 +428,76 @@ extern "C" int fv_encode_batch_opts(const fv_gmm *gmm, const void *X, int x_is_b
                        tau, cnt);
 }
 
+extern "C" int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *X, const float *xy,
+                             const int64_t *offsets, int B, int x_on_device, float *fv_out, int out_on_device,
+                             void *cuda_stream) {
+    int rc = check_common(gmm, fv_out);
+    if (rc != FV_OK) return rc;
+    if (!pca) return fail(FV_ERR_INVALID, "fv_encode_pca: NULL PCA handle");
+    if (B <= 0 || !offsets) return fail(FV_ERR_INVALID, "B must be > 0 and offsets non-NULL");
+    int m = 0, Din = 0;
+    fv_pca_info(pca, &m, &Din);
+    if (gmm->D != m + (xy ? 2 : 0))
+        return fail(FV_ERR_INVALID, "fv_encode_pca: the GMM's D must be m + 2 (m without positions)");
+    if (offsets[0] != 0) return fail(FV_ERR_INVALID, "offsets[0] must be 0");
+    for (int b = 0; b < B; ++b)
+        if (offsets[b + 1] < offsets[b]) return fail(FV_ERR_INVALID, "offsets must be non-decreasing");
+    const int64_t N = offsets[B];
+    if (N > 0 && !X) return fail(FV_ERR_INVALID, "descriptor pointer is NULL");
+    if (x_on_device && N > 0 && (!is_device_ptr(X) || (xy && !is_device_ptr(xy))))
+        return fail(FV_ERR_INVALID, "x_on_device=1 but X or xy is not device memory");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool bf16 = gmm->prec == FV_PREC_BF16;
+    const int D = gmm->D, ld = bf16 ? gmm->Dp : D;
+    Scratch s;
+    const size_t o_x = !x_on_device ? s.take(sizeof(float) * std::max<int64_t>(N, 1) * Din) : 0;
+    const size_t o_xy = (!x_on_device && xy) ? s.take(sizeof(float) * 2 * std::max<int64_t>(N, 1)) : 0;
+    const size_t o_y = s.take((bf16 ? 2 : 4) * (size_t)std::max<int64_t>(N, 1) * ld);
+    const size_t o_err = s.take(16);
+    cudaError_t e = cudaMallocAsync((void **)&s.base, s.off, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fv_encode_pca: cudaMallocAsync(scratch)");
+    const float *Xd = X, *xyd = xy;
+    uint32_t *errd = (uint32_t *)(s.base + o_err);
+    uint32_t herr = 0;
+    do {
+        if ((e = cudaMemsetAsync(errd, 0, 4, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "fv_encode_pca: memset");
+            break;
+        }
+        if (!x_on_device && N > 0) {
+            if ((e = cudaMemcpyAsync(s.base + o_x, X, sizeof(float) * N * Din, cudaMemcpyHostToDevice, st)) !=
+                    cudaSuccess ||
+                (xy && (e = cudaMemcpyAsync(s.base + o_xy, xy, sizeof(float) * 2 * N, cudaMemcpyHostToDevice, st)) !=
+                           cudaSuccess)) {
+                rc = cuda_fail(e, "fv_encode_pca: cudaMemcpyAsync(X)");
+                break;
+            }
+            Xd = (const float *)(s.base + o_x);
+            xyd = xy ? (const float *)(s.base + o_xy) : nullptr;
+        }
+        if (N > 0 && ((uintptr_t)Xd) % 16 != 0) {
+            rc = fail(FV_ERR_INVALID, "fv_encode_pca: X must be 16-byte aligned");
+            break;
+        }
+        if ((e = launch_pca(pca, Xd, xyd, N, bf16, s.base + o_y, ld, errd, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "fv_encode_pca: projection launch");
+            break;
+        }
+        rc = encode_impl(gmm, s.base + o_y, bf16, ld, offsets, B, 1, fv_out, out_on_device, st);
+        if (rc != FV_OK && rc != FV_ERR_EMPTY) break;
+        if (!out_on_device) {
+            if ((e = cudaMemcpyAsync(&herr, errd, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                rc = cuda_fail(e, "fv_encode_pca: error word");
+                break;
+            }
+            if (herr) rc = fail(FV_ERR_DEVICE, "fv_encode_pca: the projection gave up on a bounded wait");
+        }
+    } while (0);
+    cudaFreeAsync(s.base, st);
+    return rc;
+}
+
 // ---- instrumentation ------------------------------------------------------------
 namespace fv {
 namespace {

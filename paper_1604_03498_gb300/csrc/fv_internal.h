@@ -79,6 +79,8 @@ struct GmmDev {
 
 }  // namespace fv
 
+struct fv_pca;
+
 struct fv_gmm {
     int K, D;
     int Kp;     // components padded (64 for FP32, 128 for BF16)
@@ -163,6 +165,11 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 // into its first slot in the canonical order.
 cudaError_t launch_slot_reduce(const fv_gmm *g, float *part, int P, const FrameInfo *frames, int B, int max_slots,
                                cudaStream_t st);
+// PCA projection + position append (Sec. 3.1) of N rows into device Y:
+// FP32 rows of pitch D (bf16 = false) or bfloat16 rows of pitch ld (bf16 =
+// true, ld a multiple of 16); err: device word set if an MMA wait expired.
+cudaError_t launch_pca(const fv_pca *p, const float *X, const float *xy, int64_t N, bool bf16, void *Y, int ld,
+                       uint32_t *err, cudaStream_t st);
 cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments,
                             const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
                             const uint32_t *err = nullptr, const int *B_dev = nullptr, int max_slots = 1,

@@ -131,6 +131,16 @@ def lib():
             L.fv_gmm_fit.argtypes = [ctypes.POINTER(fv_gmm_desc), P, I64, I, I, ctypes.c_double, ctypes.c_double, P, P,
                                      P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double), P]
             L.fv_gmm_fit.restype = I
+            L.fv_pca_load.argtypes = [P, P, I, I, ctypes.POINTER(P)]
+            L.fv_pca_load.restype = I
+            L.fv_pca_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+            L.fv_pca_info.restype = I
+            L.fv_pca_free.argtypes = [P]
+            L.fv_pca_free.restype = None
+            L.fv_pca_project.argtypes = [P, P, P, I64, P, I, I64, P]
+            L.fv_pca_project.restype = I
+            L.fv_encode_pca.argtypes = [P, P, P, P, P, I, I, P, I, P]
+            L.fv_encode_pca.restype = I
             L.fv_encode_noalloc.argtypes = [P, P, I64, P, P]
             L.fv_encode_noalloc.restype = I
             L.fv_prof_enable.argtypes = [I]
@@ -330,6 +340,53 @@ def fv_gmm_fit(w0, mu0, var0, X, max_iter: int = 100, tol: float = 1e-3, reg_cov
                             w.ctypes.data, mu.ctypes.data, var.ctypes.data, ctypes.byref(it), ctypes.byref(ll),
                             _stream(stream)))
     return w, mu, var, it.value, ll.value
+
+
+class Pca:
+    """Owns an fv_pca handle (PCA projection + position append)."""
+
+    def __init__(self, handle, m, Din):
+        self.handle = handle
+        self.m, self.Din = m, Din
+
+    def close(self):
+        if self.handle:
+            lib().fv_pca_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fv_pca_load(basis, mean=None) -> Pca:
+    P = np.ascontiguousarray(np.asarray(basis, dtype=np.float32))
+    m, Din = P.shape
+    mn = None if mean is None else np.ascontiguousarray(np.asarray(mean, dtype=np.float32))
+    h = ctypes.c_void_p()
+    _check(lib().fv_pca_load(P.ctypes.data, None if mn is None else mn.ctypes.data, m, Din, ctypes.byref(h)))
+    return Pca(h, m, Din)
+
+
+def fv_pca_project(p: Pca, X, xy, Y, y_bf16: bool, ld_y: int = 0, stream=None) -> int:
+    """C fv_pca_project (device tensors): Y receives the projected rows."""
+    xp, _ = _ptr(X)
+    yp, _ = _ptr(Y)
+    xyp = _ptr(xy)[0] if xy is not None else None
+    return _check(lib().fv_pca_project(p.handle, xp, xyp, int(X.shape[0]), yp, int(bool(y_bf16)), int(ld_y),
+                                       _stream(stream)), (FV_OK,))
+
+
+def fv_encode_pca(g: Gmm, p: Pca, X, xy, offsets, out, stream=None, allow=(FV_OK, FV_ERR_EMPTY)) -> int:
+    """C fv_encode_pca: X (N x Din) and xy (N x 2 or None) on the same side."""
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    xp, xd = _ptr(X)
+    xyp = _ptr(xy)[0] if xy is not None else None
+    op, od = _ptr(out)
+    return _check(lib().fv_encode_pca(g.handle, p.handle, xp, xyp, offs.ctypes.data, offs.size - 1, xd, op, od,
+                                      _stream(stream)), allow)
 
 
 class BatchPlan:
