@@ -135,3 +135,26 @@ def sample_positions(N: int, seed: int = 0) -> np.ndarray:
     """Normalised (x, y) positions of N descriptors, Uniform(-0.5, 0.5)^2."""
     g = _rng(STREAM_IMAGES, seed, N)
     return np.ascontiguousarray(g.uniform(-0.5, 0.5, size=(N, 2)), dtype=np.float32)
+
+
+def make_frames(B: int, H: int = 240, W: int = 320, seed: int = 0) -> np.ndarray:
+    """B grey-level frames (float32, B x H x W, values in [0, 1]) with the
+    structure dense SIFT responds to: 24 Gaussian blobs of random position,
+    width (4-40 px) and sign, 3 oriented gratings of random period (8-48 px)
+    and angle, and pixel noise of standard deviation 0.02, rescaled to [0, 1]."""
+    g = _rng(STREAM_IMAGES, seed, B, H, W)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    out = np.empty((B, H, W), np.float32)
+    for b in range(B):
+        img = np.zeros((H, W))
+        for _ in range(24):
+            cy, cx = g.uniform(0, H), g.uniform(0, W)
+            sd = g.uniform(4, 40)
+            img += g.choice([-1.0, 1.0]) * g.uniform(0.3, 1.0) * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * sd * sd))
+        for _ in range(3):
+            th, per = g.uniform(0, np.pi), g.uniform(8, 48)
+            img += 0.3 * np.sin(2 * np.pi * (np.cos(th) * xx + np.sin(th) * yy) / per + g.uniform(0, 2 * np.pi))
+        img += g.normal(0, 0.02, size=(H, W))
+        img = (img - img.min()) / max(img.max() - img.min(), 1e-12)
+        out[b] = img
+    return out
