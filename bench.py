@@ -429,6 +429,67 @@ def pca_form(args, stream, barrier, dist, world, hbm_peak):
     return res
 
 
+def images_form(args, stream, barrier, dist, world):
+    """Images in, Fisher vectors out: dense SIFT over the 8-scale pyramid
+    (stride 4, 4x4x8 bins), PCA to 62 + (x, y), encoding against a K=256 GMM,
+    on 320x240 synthetic frames, 16 frames per fv_encode_images call; the
+    workload of the paper's per-frame time (34 ms per 320x240 frame for dense
+    SIFT + FV on a K40, context only). Dense SIFT alone is timed beside it and
+    its descriptors are checked against the oracle on one frame."""
+    import torch
+    from paper_1604_03498_gb300 import fv
+    import oracle
+    from oracle import dsift_oracle as O
+    B, H, W, m, K = 16, 240, 320, 62, 256
+    frames = synth.make_frames(64, H, W, seed=11)
+    fd = torch.from_numpy(frames).cuda()
+    P, mean = synth.make_pca(128, m, seed=11)
+    w, mu, var = synth.make_gmm(K, m + 2, seed=11)
+    mu, var = (0.3 * mu).astype(np.float32), (0.05 * var).astype(np.float32)
+    pca = fv.fv_pca_load(P, mean)
+    n = fv.fv_dsift_count(H, W)
+    desc = torch.zeros(B, n, 128, device="cuda")
+    xy = torch.zeros(B, n, 2, device="cuda")
+    res = {"workload": f"320x240 frames, dense SIFT (8 scales, stride 4) -> {n} descriptors per frame -> "
+                       f"PCA {m} + (x, y) -> K={K}; {B} frames per call, a 64-frame pool",
+           "paper_context_ms_per_frame": 34.0}
+    steps = max(3, min(args.steps, 20))
+
+    def dsift_step():
+        for c in range(64 // B):
+            fv.fv_dsift(fd[c * B:(c + 1) * B], desc, xy, stream=stream.cuda_stream)
+
+    for _ in range(max(3, args.warmup)):
+        dsift_step()
+    torch.cuda.synchronize()
+    ms, _ = timed(dsift_step, steps, stream, barrier, dist)
+    res["dsift_ms_per_frame"] = ms / (steps * 64)
+    dh = desc[0].cpu().numpy()
+    D, _ = O.dense_sift(frames[0].astype(np.float64))
+    res["dsift_max_abs_err_vs_oracle"] = float(np.abs(dh - D).max())
+    for tag, prec in (("fp32", fv.FV_PREC_FP32), ("bf16", fv.FV_PREC_BF16)):
+        g = fv.fv_gmm_load(w, mu, var, prec)
+        out = torch.zeros(64, 2 * K * (m + 2), device="cuda")
+
+        def step():
+            for c in range(64 // B):
+                fv.fv_encode_images(g, pca, fd[c * B:(c + 1) * B], out[c * B:(c + 1) * B], stream=stream.cuda_stream)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ms, launches = timed(step, steps, stream, barrier, dist)
+        Y = oracle.pca_project(D, P, mean, O.dense_sift(frames[0].astype(np.float64))[1])
+        Yin = Y if prec == fv.FV_PREC_FP32 else synth.to_bf16_grid(Y.astype(np.float32))
+        err = float(np.abs(out[0].cpu().numpy() - oracle.encode(Yin, w, mu, var)["fv"]).max())
+        res[tag] = {"frames_per_s": world * steps * 64 / (ms / 1e3), "ms_per_frame": ms / (steps * 64),
+                    "descriptors_per_s": world * steps * 64 * n / (ms / 1e3), "gpu_launches": launches,
+                    "max_abs_err_vs_oracle": err}
+        g.close()
+    pca.close()
+    return res
+
+
 def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, pool_f32, stream, barrier, dist, world, tc_peak, work_bf,
                        issued_bf, tc_sustained):
     """256 frames with N ~ Uniform{5000..40000} (D=64, K=256, bf16 descriptors
@@ -831,6 +892,9 @@ def main():
 
     # ---- raw descriptors through the PCA + position prologue ----
     forms["pca_encode"] = pca_form(args, stream, barrier, dist, world, float(peaks.get("hbm_gbs", 6800.0)))
+
+    # ---- images in, Fisher vectors out: dense SIFT -> PCA -> encoder ----
+    forms["images_encode"] = images_form(args, stream, barrier, dist, world)
 
     # ---- GMM training by EM on the same frames ----
     forms["gmm_em"] = em_form(args, w, mu, var, frames, Xd, stream, barrier, dist, world)

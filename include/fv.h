@@ -218,6 +218,49 @@ FV_API int fv_pca_project(const fv_pca *pca, const float *X, const float *xy, in
 FV_API int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *X, const float *xy, const int64_t *offsets,
                          int B, int x_on_device, float *fv_out, int out_on_device, void *cuda_stream);
 
+/* ---- dense SIFT: the descriptors of an image (Sec. 3.1-3.2, Sec. 4) ----------
+ * Flat-window dense SIFT on the GPU over an image pyramid:
+ *   scales s_j = 2^((top_scale - j)/2), j < n_scales (the paper's 8 scales
+ *   from sqrt 2 down to 1/8: top_scale 1, n_scales 8; its 9-scale setting:
+ *   top_scale 2, n_scales 9), each floor(H s + 1/2) x floor(W s + 1/2) pixels
+ *   resampled bilinearly; central-difference gradients (one-sided on the
+ *   border); each gradient's magnitude split linearly between its two nearest
+ *   of 8 orientation bins; the triangular filter k(d) = 1 - |d|/b (2b - 1
+ *   taps) along x then y, each output summing its inputs directly and only
+ *   at the pixels the descriptors read (Sec. 3.2); 4 x 4 spatial bins of
+ *   b x b pixels x 8 orientations = 128 entries, entry (4 by + bx) 8 + o, on a
+ *   grid of centres x0 = 2b + stride i <= W_s - 2b (likewise y0); each
+ *   descriptor L2-normalised, capped at 0.2 and renormalised (zero stays
+ *   zero); positions (x0 / W_s - 0.5, y0 / H_s - 0.5). Descriptors of an
+ *   image come scale by scale, row-major by (y0, x0) within a scale. */
+typedef struct {
+    int bin_size;    /* b: even, 2..16 (default 4) */
+    int stride;      /* grid spacing in pixels; must divide bin_size (default 4, Sec. 4) */
+    int n_scales;    /* 1..9 (default 8) */
+    int top_scale;   /* the largest scale is 2^(top_scale/2) (default 1: sqrt 2) */
+} fv_dsift_params;
+
+/* Descriptors per image of size H x W (params NULL = the defaults above).
+ * Errors: FV_ERR_INVALID for parameters or sizes outside the ranges. */
+FV_API int fv_dsift_count(int H, int W, const fv_dsift_params *params, int64_t *n_per_image);
+
+/* Dense SIFT of B grey-level images (B x H x W float32, row-major, host or
+ * device per images_on_device) into desc (DEVICE, B x n x 128 float32,
+ * 16-byte aligned) and xy (DEVICE, B x n x 2 float32, or NULL), n from
+ * fv_dsift_count. Stream-ordered. Errors: FV_ERR_INVALID, FV_ERR_EMPTY (no
+ * descriptor fits the image), FV_ERR_OOM, FV_ERR_CUDA. */
+FV_API int fv_dsift(const float *images, int B, int H, int W, int images_on_device, const fv_dsift_params *params,
+                    float *desc, float *xy, void *cuda_stream);
+
+/* Images in, Fisher vectors out: fv_dsift, then fv_encode_pca with the
+ * descriptors and positions of each image as one frame (the PCA takes
+ * 128-dimensional descriptors; the GMM's D must be m + 2). fv_out: B x 2KD,
+ * host or device per out_on_device. Every intermediate stays on the device.
+ * Errors as fv_dsift and fv_encode_pca. */
+FV_API int fv_encode_images(const fv_gmm *gmm, const fv_pca *pca, const float *images, int B, int H, int W,
+                            int images_on_device, const fv_dsift_params *params, float *fv_out, int out_on_device,
+                            void *cuda_stream);
+
 /* ---- GMM training: expectation-maximisation on the GPU -----------------------
  * The paper encodes with a GMM trained beforehand (Sec. 3.1). These calls
  * train one on the GPU with the encoder's own kernels: the E-step is the

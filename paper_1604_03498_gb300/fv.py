@@ -52,6 +52,11 @@ class fv_encode_options(ctypes.Structure):
     _fields_ = [("posterior_threshold", ctypes.c_float), ("skip_counts", ctypes.c_void_p)]
 
 
+class fv_dsift_params(ctypes.Structure):
+    _fields_ = [("bin_size", ctypes.c_int), ("stride", ctypes.c_int), ("n_scales", ctypes.c_int),
+                ("top_scale", ctypes.c_int)]
+
+
 class fv_batch_plan_config(ctypes.Structure):
     _fields_ = [("max_frames", ctypes.c_int), ("max_rows", ctypes.c_int64), ("autotune", ctypes.c_int),
                 ("tune_cache", ctypes.c_char_p)]
@@ -141,6 +146,12 @@ def lib():
             L.fv_pca_project.restype = I
             L.fv_encode_pca.argtypes = [P, P, P, P, P, I, I, P, I, P]
             L.fv_encode_pca.restype = I
+            L.fv_dsift_count.argtypes = [I, I, ctypes.POINTER(fv_dsift_params), ctypes.POINTER(I64)]
+            L.fv_dsift_count.restype = I
+            L.fv_dsift.argtypes = [P, I, I, I, I, ctypes.POINTER(fv_dsift_params), P, P, P]
+            L.fv_dsift.restype = I
+            L.fv_encode_images.argtypes = [P, P, P, I, I, I, I, ctypes.POINTER(fv_dsift_params), P, I, P]
+            L.fv_encode_images.restype = I
             L.fv_encode_noalloc.argtypes = [P, P, I64, P, P]
             L.fv_encode_noalloc.restype = I
             L.fv_prof_enable.argtypes = [I]
@@ -387,6 +398,35 @@ def fv_encode_pca(g: Gmm, p: Pca, X, xy, offsets, out, stream=None, allow=(FV_OK
     op, od = _ptr(out)
     return _check(lib().fv_encode_pca(g.handle, p.handle, xp, xyp, offs.ctypes.data, offs.size - 1, xd, op, od,
                                       _stream(stream)), allow)
+
+
+def _dsift_params(bin_size=4, stride=4, n_scales=8, top_scale=1):
+    return fv_dsift_params(int(bin_size), int(stride), int(n_scales), int(top_scale))
+
+
+def fv_dsift_count(H: int, W: int, **params) -> int:
+    n = ctypes.c_int64()
+    _check(lib().fv_dsift_count(int(H), int(W), ctypes.byref(_dsift_params(**params)), ctypes.byref(n)))
+    return n.value
+
+
+def fv_dsift(images, desc, xy=None, stream=None, **params) -> int:
+    """C fv_dsift: images (B x H x W float32, host or CUDA) -> desc (CUDA,
+    B x n x 128) and xy (CUDA, B x n x 2, optional)."""
+    B, H, W = (int(v) for v in images.shape)
+    ip, idv = _ptr(images)
+    dp, _ = _ptr(desc)
+    xp = _ptr(xy)[0] if xy is not None else None
+    return _check(lib().fv_dsift(ip, B, H, W, idv, ctypes.byref(_dsift_params(**params)), dp, xp, _stream(stream)))
+
+
+def fv_encode_images(g: Gmm, p: "Pca", images, out, stream=None, allow=(FV_OK,), **params) -> int:
+    """C fv_encode_images: images (B x H x W) -> out (B x 2KD)."""
+    B, H, W = (int(v) for v in images.shape)
+    ip, idv = _ptr(images)
+    op, od = _ptr(out)
+    return _check(lib().fv_encode_images(g.handle, p.handle, ip, B, H, W, idv, ctypes.byref(_dsift_params(**params)),
+                                         op, od, _stream(stream)), allow)
 
 
 class BatchPlan:
