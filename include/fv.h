@@ -65,8 +65,12 @@ typedef enum {
 } fv_status;
 
 typedef enum {
-    FV_PREC_FP32 = 0,  /* plain FP32 form: SIMT kernels, centred statistics */
-    FV_PREC_BF16 = 1   /* precision form: BF16 tensor-core GEMMs, hi+lo split */
+    FV_PREC_FP32 = 0,    /* plain FP32 form: SIMT kernels, centred statistics */
+    FV_PREC_BF16 = 1,    /* precision form: BF16 tensor-core GEMMs, hi+lo split */
+    FV_PREC_BF16X2 = 2   /* the precision form with the posteriors entering the
+                            statistics GEMM as bf16 hi + lo pairs (about 2^-16
+                            relative instead of 2^-9): the accurate choice when a
+                            component's 1/sqrt(w) is large; one Y stage, slower */
 } fv_precision;
 
 /* GMM parameters, all host memory, float32:

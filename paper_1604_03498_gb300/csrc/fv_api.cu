@@ -240,7 +240,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     if (out_on_device && !is_device_ptr(fv_out)) return fail(FV_ERR_INVALID, "out_on_device=1 but fv_out is not device memory");
 
     const int sms = device_sms(g->device);
-    const bool bf16 = g->prec == FV_PREC_BF16;
+    const bool bf16 = is_bf16(g->prec);
 
     Plan plan;
     if (bf16) {
@@ -399,7 +399,7 @@ extern "C" int fv_encode_batch_bf16(const fv_gmm *gmm, const uint16_t *X_bf16, i
                                     int B, float *fv_out, void *cuda_stream) {
     int rc = check_common(gmm, fv_out);
     if (rc != FV_OK) return rc;
-    if (gmm->prec != FV_PREC_BF16) return fail(FV_ERR_INVALID, "fv_encode_batch_bf16 needs an FV_PREC_BF16 GMM");
+    if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_encode_batch_bf16 needs an FV_PREC_BF16 GMM");
     if (B <= 0 || !offsets) return fail(FV_ERR_INVALID, "B must be > 0 and offsets non-NULL");
     if (ld_x < gmm->D || ld_x % 8 != 0) return fail(FV_ERR_INVALID, "ld_x must be >= D and a multiple of 8");
     if (((uintptr_t)X_bf16) % 16 != 0) return fail(FV_ERR_INVALID, "X_bf16 must be 16-byte aligned");
@@ -417,7 +417,7 @@ extern "C" int fv_encode_batch_opts(const fv_gmm *gmm, const void *X, int x_is_b
     unsigned long long *cnt = opts ? (unsigned long long *)opts->skip_counts : nullptr;
     if (cnt && !is_device_ptr(cnt)) return fail(FV_ERR_INVALID, "skip_counts must be device memory");
     if (x_is_bf16) {
-        if (gmm->prec != FV_PREC_BF16) return fail(FV_ERR_INVALID, "bfloat16 descriptors need an FV_PREC_BF16 GMM");
+        if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "bfloat16 descriptors need an FV_PREC_BF16 GMM");
         if (!x_on_device || !out_on_device)
             return fail(FV_ERR_INVALID, "bfloat16 descriptors and their output must be device memory");
         if (ld_x < gmm->D || ld_x % 8 != 0) return fail(FV_ERR_INVALID, "ld_x must be >= D and a multiple of 8");
@@ -447,7 +447,7 @@ extern "C" int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *
     if (x_on_device && N > 0 && (!is_device_ptr(X) || (xy && !is_device_ptr(xy))))
         return fail(FV_ERR_INVALID, "x_on_device=1 but X or xy is not device memory");
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const bool bf16 = gmm->prec == FV_PREC_BF16;
+    const bool bf16 = is_bf16(gmm->prec);
     const int D = gmm->D, ld = bf16 ? gmm->Dp : D;
     Scratch s;
     const size_t o_x = !x_on_device ? s.take(sizeof(float) * std::max<int64_t>(N, 1) * Din) : 0;

@@ -26,6 +26,14 @@
 //    per-block copies of the statistics).
 // The finalise kernel centres the raw moments, scales and normalises.
 //
+// FV_PREC_BF16X2: the posteriors enter the statistics GEMM as a bf16 hi + lo
+// pair (gamma = hi + lo to about 2^-16, two MMAs per K step into the same
+// accumulator), so the statistics carry the posteriors' FP32 values instead
+// of their bfloat16 rounding (2^-9 relative). That rounding is the largest
+// error of the precision form, and the improved-FV scaling 1/(N sqrt(w))
+// magnifies it for components of very small prior w. The doubled gamma^T tile
+// leaves room for one Y stage at D = 64 (two at D <= 48).
+//
 // Early termination (Sec. 3.3, Algorithm 5), as block sparsity of the
 // statistics GEMM: with a posterior threshold tau > 0 the softmax writes
 // posteriors not above tau as zeros and marks each 16-row K step of the
@@ -115,6 +123,7 @@ struct EncArgs {
     const int2 *cl_units;     // per cluster: (first unit, number of units)
     float *part;              // [slot][P][Kp] statistics slots
     uint32_t *err;
+    int glo;                  // 1: posteriors as bf16 hi + lo (FV_PREC_BF16X2)
     float tau;                // posterior threshold (0: exact, every MMA issued)
     unsigned long long *skip_count;   // [skipped, issued + skipped] statistics K steps (nullable)
 };
@@ -124,7 +133,7 @@ struct EncSmem {
     uint32_t b, xr, y, y_stage, g, hx, xchg, cl, bars, misc, flags, total;
 };
 
-__host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage) {
+__host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage, bool glo = false) {
     EncSmem s;
     uint32_t off = 0;
     s.b = off;                                   // [Qh | Ql | Rh | Rl] x nkb blocks of 128 components
@@ -134,8 +143,8 @@ __host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage) {
     s.y_stage = (3u * nkb + 1u) * kBlk;          // [X | X2hi | X2lo | 1] blocks of 128 rows
     s.y = off;
     off += nstage * s.y_stage;
-    s.g = off;                                   // gamma^T: two 64-component halves
-    off += 2u * kGHalf;
+    s.g = off;                                   // gamma^T: two 64-component halves (then the lo pair's)
+    off += (glo ? 4u : 2u) * kGHalf;
     s.hx = off;                                  // (max, sum) per row of each column half
     off += 2u * kRows * 8u;
     s.xchg = off;                                // (max, sum) per row: 2 slots x S ranks
@@ -276,11 +285,14 @@ struct TileWalk {
     __device__ int slot() const { return slot_; }
 };
 
+// SPARSE: early termination with p.tau > 0 (a separate instantiation, so the
+// exact encoder's code is the same as without it).
+template <bool SPARSE, bool GLO>
 __global__ void __launch_bounds__(kThreads, 1)
 bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, EncArgs p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const EncSmem L = enc_smem(p.nkb, p.S, p.nstage);
+    const EncSmem L = enc_smem(p.nkb, p.S, p.nstage, GLO);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);   // [0] tmem base, [1] abort
     volatile uint32_t *abort_flag = misc + 1;
@@ -399,7 +411,6 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         const uint32_t idesc_s = idesc_bf16(kComps, p.ny, true, true);
         const uint32_t sG = smem_u32(smem + L.g);
         const volatile uint8_t *flags = smem + L.flags;
-        const bool sparse = p.tau > 0.f;
         bool issued = false, started = false;
         unsigned long long nskip = 0, nsteps = 0;
         int i = 0;
@@ -409,26 +420,36 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             }
             if (!mbar_wait(&bars[EB_GFULL], i & 1, abort_flag, p.err)) break;
             tc_fence_after();
-            if (w.first()) started = false;   // the next MMA initialises the unit's accumulator
             const uint32_t sy = smem_u32(smem + L.y + (i % p.nstage) * L.y_stage);
-            for (int q = 0; q < kRows / 16; ++q) {
-                // a K step whose 16 x 128 posteriors are all zero adds nothing;
-                // a unit's last tile issues its first step regardless when
-                // nothing was issued yet (zero posteriors then zero the accumulator)
-                if (sparse) {
+            if constexpr (SPARSE) {
+                if (w.first()) started = false;   // the next MMA initialises the unit's accumulator
+                for (int q = 0; q < kRows / 16; ++q) {
+                    // a K step whose 16 x 128 posteriors are all zero adds nothing;
+                    // a unit's last tile issues its first step regardless when
+                    // nothing was issued yet (zero posteriors then zero the accumulator)
                     ++nsteps;
                     if (!(flags[q] | flags[8 + q]) && (started || !w.last() || q > 0)) {
                         ++nskip;
                         continue;
                     }
+                    const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
+                    const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                    mma_bf16(tmem + kStatCol, a, b, idesc_s, started ? 1u : 0u);
+                    if constexpr (GLO)
+                        mma_bf16(tmem + kStatCol, sdesc_sw128(sG + 2 * kGHalf + q * 2048, kGHalf, 1024), b, idesc_s, 1u);
+                    started = true;
                 }
-                // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
-                // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
-                // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
-                const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
-                const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
-                mma_bf16(tmem + kStatCol, a, b, idesc_s, started ? 1u : 0u);
-                started = true;
+            } else {
+                for (int q = 0; q < kRows / 16; ++q) {
+                    // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
+                    // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
+                    // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
+                    const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
+                    const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                    mma_bf16(tmem + kStatCol, a, b, idesc_s, (w.first() && q == 0) ? 0u : 1u);
+                    if constexpr (GLO)   // the lo halves of the posteriors, same Y planes
+                        mma_bf16(tmem + kStatCol, sdesc_sw128(sG + 2 * kGHalf + q * 2048, kGHalf, 1024), b, idesc_s, 1u);
+                }
             }
             mma_commit(&bars[EB_GFREE]);
             mma_commit(&bars[EB_STFREE + (i & 1)]);
@@ -439,7 +460,7 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             mma_commit(&bars[EB_DRAIN2]);
             mbar_drain(&bars[EB_DRAIN2], 0, 2000000000ll);
         }
-        if (sparse && p.skip_count) {
+        if (SPARSE && p.skip_count) {
             atomicAdd(&p.skip_count[0], nskip);
             atomicAdd(&p.skip_count[1], nsteps);
         }
@@ -613,14 +634,14 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             // pass B: normalised posteriors -> bf16 gamma^T (second chunk's load in flight)
             tmem_ld32_issue(ta, ra);
             tmem_ld_wait(ra);
-            const float tau = p.tau;
             bool row_nz = false;   // early termination: a posterior of this row and half above tau
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 uint32_t(&cur)[32] = c ? rb : ra;
                 if (c == 0) tmem_ld32_issue(ta + 32, rb);
                 const float sc = ex2_approx(mc[c] - Mref) * inv;
-                if (tau > 0.f) {   // posteriors not above tau are dropped
+                if constexpr (SPARSE) {   // posteriors not above tau are dropped
+                    const float tau = p.tau;
 #pragma unroll
                     for (int k = 0; k < 32; ++k) {
                         const float g = __uint_as_float(cur[k]) * sc;
@@ -630,16 +651,32 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {   // 16-byte chunk c * 4 + k of the 128-byte row
-                    uint4 v;
-                    v.x = pack_bf16x2(__uint_as_float(cur[8 * k + 0]) * sc, __uint_as_float(cur[8 * k + 1]) * sc);
-                    v.y = pack_bf16x2(__uint_as_float(cur[8 * k + 2]) * sc, __uint_as_float(cur[8 * k + 3]) * sc);
-                    v.z = pack_bf16x2(__uint_as_float(cur[8 * k + 4]) * sc, __uint_as_float(cur[8 * k + 5]) * sc);
-                    v.w = pack_bf16x2(__uint_as_float(cur[8 * k + 6]) * sc, __uint_as_float(cur[8 * k + 7]) * sc);
-                    *reinterpret_cast<uint4 *>(gsm + (((c * 4 + k) ^ sw) << 4)) = v;
+                    if constexpr (GLO) {
+                        // hi = RN_bf16(g), lo = RN_bf16(g - hi): g - hi is exact in FP32
+                        uint32_t hv[4], lv[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float g0 = __uint_as_float(cur[8 * k + 2 * e]) * sc;
+                            const float g1 = __uint_as_float(cur[8 * k + 2 * e + 1]) * sc;
+                            hv[e] = pack_bf16x2(g0, g1);
+                            const float h0 = __uint_as_float(hv[e] << 16), h1 = __uint_as_float(hv[e] & 0xFFFF0000u);
+                            lv[e] = pack_bf16x2(g0 - h0, g1 - h1);
+                        }
+                        *reinterpret_cast<uint4 *>(gsm + (((c * 4 + k) ^ sw) << 4)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *reinterpret_cast<uint4 *>(gsm + 2 * kGHalf + (((c * 4 + k) ^ sw) << 4)) =
+                            make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    } else {
+                        uint4 v;
+                        v.x = pack_bf16x2(__uint_as_float(cur[8 * k + 0]) * sc, __uint_as_float(cur[8 * k + 1]) * sc);
+                        v.y = pack_bf16x2(__uint_as_float(cur[8 * k + 2]) * sc, __uint_as_float(cur[8 * k + 3]) * sc);
+                        v.z = pack_bf16x2(__uint_as_float(cur[8 * k + 4]) * sc, __uint_as_float(cur[8 * k + 5]) * sc);
+                        v.w = pack_bf16x2(__uint_as_float(cur[8 * k + 6]) * sc, __uint_as_float(cur[8 * k + 7]) * sc);
+                        *reinterpret_cast<uint4 *>(gsm + (((c * 4 + k) ^ sw) << 4)) = v;
+                    }
                 }
                 if (c == 0) tmem_ld_wait(rb);
             }
-            if (tau > 0.f) {   // marks of this warp's two 16-row K steps (its half of the components)
+            if constexpr (SPARSE) {   // marks of this warp's two 16-row K steps (its half of the components)
                 const uint32_t bal = __ballot_sync(0xffffffffu, row_nz);
                 if (lane == 0) {
                     smem[L.flags + h * 8 + 2 * q] = (bal & 0xFFFFu) != 0u;
@@ -728,6 +765,7 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, ui
 
 struct EncCfg {
     int nkb, S, nstage, ny;
+    bool glo;
     size_t smem;
 };
 
@@ -735,8 +773,9 @@ bool enc_config(const fv_gmm *g, EncCfg &c) {
     c.nkb = round_up(g->D, 16) / 16;
     c.S = g->Kp / kComps;
     c.ny = 3 * c.nkb * 16 + 16;
-    c.nstage = enc_smem(c.nkb, c.S, 2).total <= (uint32_t)kMaxSmem ? 2 : 1;
-    c.smem = enc_smem(c.nkb, c.S, c.nstage).total;
+    c.glo = g->prec == FV_PREC_BF16X2;
+    c.nstage = enc_smem(c.nkb, c.S, 2, c.glo).total <= (uint32_t)kMaxSmem ? 2 : 1;
+    c.smem = enc_smem(c.nkb, c.S, c.nstage, c.glo).total;
     return g->Kp % kComps == 0 && c.S >= 1 && c.S <= 4 && c.ny <= 256 && c.nkb * kRows * 2 <= kHold * kBuilders &&
            c.smem <= (size_t)kMaxSmem;
 }
@@ -768,7 +807,7 @@ int bf16_max_shares(const fv_gmm *g, int sms) {
     static std::map<std::tuple<int, int, size_t>, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, c.S, c.smem);
+    const auto key = std::make_tuple(dev, c.S + (c.glo ? 1000 : 0), c.smem);
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
@@ -776,9 +815,9 @@ int bf16_max_shares(const fv_gmm *g, int sms) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     enc_launch_config(c, std::max(1, sms / c.S), nullptr, cfg, attr);
-    if (cudaFuncSetAttribute(bf16_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveClusters(&n, bf16_encode_kernel, &cfg) != cudaSuccess || n < 1) {
+    auto kern = c.glo ? bf16_encode_kernel<false, true> : bf16_encode_kernel<false, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
         cudaGetLastError();
         n = std::max(1, sms / c.S);
     }
@@ -831,16 +870,19 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     a.cl_units = cl_units;
     a.part = part;
     a.err = err;
+    a.glo = c.glo ? 1 : 0;
     a.tau = tau;
     a.skip_count = skip_count;
-    cudaError_t e = cudaFuncSetAttribute(bf16_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    auto kern = tau > 0.f ? (c.glo ? bf16_encode_kernel<true, true> : bf16_encode_kernel<true, false>)
+                          : (c.glo ? bf16_encode_kernel<false, true> : bf16_encode_kernel<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return cuda_fail(e, "bf16 encoder: smem attribute");
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     enc_launch_config(c, n_shares, st, cfg, attr);
     {
         KernelTimer kt_("bf16_encode", st);
-        e = cudaLaunchKernelEx(&cfg, bf16_encode_kernel, tmX, tmB, a);
+        e = cudaLaunchKernelEx(&cfg, kern, tmX, tmB, a);
     }
     if (e != cudaSuccess) return cuda_fail(e, "bf16 encoder launch");
     return FV_OK;

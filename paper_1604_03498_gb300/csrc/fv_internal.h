@@ -44,8 +44,11 @@ constexpr int kMaxK_F32 = 512;    // posteriors keep a BM x Kp row block in shar
 constexpr int kMaxD_F32 = 1024;
 constexpr int kMaxK_BF16 = 512;   // one 128-lane x K-column TMEM accumulator
 constexpr int kMaxD_BF16 = 80;    // stats GEMM N = 3D + 16 <= 256
+constexpr int kMaxD_BF16X2 = 64;  // hi + lo posteriors: the doubled gamma^T tile fits shared memory up to D = 64
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+// The tensor-core forms (FV_PREC_BF16 and FV_PREC_BF16X2) share operands and kernels.
+inline bool is_bf16(int prec) { return prec == FV_PREC_BF16 || prec == FV_PREC_BF16X2; }
 inline int64_t round_up64(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 // ---- GMM handle ------------------------------------------------------------

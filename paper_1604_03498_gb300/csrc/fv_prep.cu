@@ -150,9 +150,9 @@ extern "C" int fv_limits(fv_precision precision, int *max_K, int *max_D) {
         if (max_D) *max_D = kMaxD_F32;
         return FV_OK;
     }
-    if (precision == FV_PREC_BF16) {
+    if (is_bf16(precision)) {
         if (max_K) *max_K = kMaxK_BF16;
-        if (max_D) *max_D = kMaxD_BF16;
+        if (max_D) *max_D = precision == FV_PREC_BF16X2 ? kMaxD_BF16X2 : kMaxD_BF16;
         return FV_OK;
     }
     return fail(FV_ERR_INVALID, "fv_limits: unknown precision");
@@ -165,7 +165,7 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
         return fail(FV_ERR_INVALID, "fv_gmm_load: NULL descriptor or parameter array");
     const int K = desc->K, D = desc->D;
     if (K <= 0 || D <= 0) return fail(FV_ERR_INVALID, "fv_gmm_load: K and D must be positive");
-    if (precision != FV_PREC_FP32 && precision != FV_PREC_BF16)
+    if (precision != FV_PREC_FP32 && !is_bf16(precision))
         return fail(FV_ERR_INVALID, "fv_gmm_load: unknown precision");
     int mK = 0, mD = 0;
     fv_limits(precision, &mK, &mD);
@@ -189,8 +189,8 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     g->K = K;
     g->D = D;
     g->prec = precision;
-    g->Kp = precision == FV_PREC_BF16 ? round_up(K, 128) : round_up(K, 64);
-    g->Dp = precision == FV_PREC_BF16 ? round_up(D, 16) : round_up(D, 8);
+    g->Kp = is_bf16(precision) ? round_up(K, 128) : round_up(K, 64);
+    g->Dp = is_bf16(precision) ? round_up(D, 16) : round_up(D, 8);
     cudaGetDevice(&g->device);
     const int Kp = g->Kp, Dp = g->Dp, D16 = round_up(D, 16);
 
@@ -203,7 +203,7 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     const size_t o_alpha = take(sizeof(float) * Kp), o_beta = take(sizeof(float) * Kp);
     const size_t o_mu = take(sizeof(float) * D * Kp), o_prec = take(sizeof(float) * D * Kp);
     size_t o_bimg = 0, o_cfull = 0, o_cl2 = 0;
-    if (precision == FV_PREC_BF16) {
+    if (is_bf16(precision)) {
         o_bimg = take(sizeof(uint16_t) * 4 * Kp * D16);
         o_cfull = take(sizeof(float) * Kp);
         o_cl2 = take(sizeof(float) * Kp);
@@ -228,9 +228,9 @@ extern "C" int fv_gmm_load(const fv_gmm_desc *desc, fv_precision precision, fv_g
     d.beta = (float *)(base + o_beta);
     d.mu_t = (float *)(base + o_mu);
     d.prec_t = (float *)(base + o_prec);
-    d.bimg = precision == FV_PREC_BF16 ? (uint16_t *)(base + o_bimg) : nullptr;
-    d.cfull = precision == FV_PREC_BF16 ? (float *)(base + o_cfull) : nullptr;
-    d.cl2 = precision == FV_PREC_BF16 ? (float *)(base + o_cl2) : nullptr;
+    d.bimg = is_bf16(precision) ? (uint16_t *)(base + o_bimg) : nullptr;
+    d.cfull = is_bf16(precision) ? (float *)(base + o_cfull) : nullptr;
+    d.cl2 = is_bf16(precision) ? (float *)(base + o_cl2) : nullptr;
     float *in = (float *)(base + o_in);
     d.params = in;
 

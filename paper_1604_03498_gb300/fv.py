@@ -32,6 +32,7 @@ FV_ERR_UNSUPPORTED = -9
 
 FV_PREC_FP32 = 0
 FV_PREC_BF16 = 1
+FV_PREC_BF16X2 = 2
 
 _lock = threading.Lock()
 _lib = None

@@ -4,7 +4,7 @@ import numpy as np
 import oracle
 from paper_1604_03498_gb300 import fv, synth
 
-TOL = {fv.FV_PREC_FP32: 1e-4, fv.FV_PREC_BF16: 2e-3}
+TOL = {fv.FV_PREC_FP32: 1e-4, fv.FV_PREC_BF16: 2e-3, fv.FV_PREC_BF16X2: 2e-3}
 
 
 def torch_cuda():

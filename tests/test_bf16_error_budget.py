@@ -42,7 +42,7 @@ def budget(request):
     def err(**kw):
         return float(np.abs(E.encode(X, w, mu, var, **kw) - ref).max())
 
-    out = {"kernel": err(), "exact_gamma": err(gamma="exact")}
+    out = {"kernel": err(), "exact_gamma": err(gamma="exact"), "hilo_gamma": err(gamma="hilo")}
     for t in TERMS:
         out["-" + t] = err(drop=(t,))
     return out
@@ -60,3 +60,9 @@ def test_every_split_term_is_needed(budget, term):
 
 def test_posterior_rounding_dominates_the_remaining_error(budget):
     assert budget["exact_gamma"] <= budget["kernel"] / 4, budget
+
+
+def test_hi_lo_posteriors_remove_the_posterior_rounding(budget):
+    """FV_PREC_BF16X2 keeps the posteriors as bf16 hi + lo in the statistics
+    GEMM: its error is that of exact posteriors."""
+    assert budget["hilo_gamma"] <= 1.05 * budget["exact_gamma"] + 1e-7, budget
