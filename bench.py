@@ -564,7 +564,9 @@ def batched_graph_form(args, gbf, w, mu, var, Xpool_bf16, pool_f32, stream, barr
          "us_per_frame": 1e3 * ms / (steps * B), "frames_per_launch": B, "rows_per_launch": rows,
          "ms_per_graph_launch": per_launch_ms, "gpu_launches": launches, "steps": steps,
          "frame_sizes": "Uniform{5000..40000}, seed 4", "output_finite_unit_norm": ok, "error": err,
-         "autotune": {"stat_ctas": info["stat_ctas"], "tuned": info["tuned"], "tuned_ms": info["tuned_ms"],
+         "autotune": {"shares": info["stat_ctas"], "rows_per_tile": info["rows_per_tile"],
+                      "y_stages": info["y_stages"], "tiles_per_share": info["tiles_per_share"],
+                      "candidates_timed": info["candidates"], "tuned": info["tuned"], "tuned_ms": info["tuned_ms"],
                       "plan_create_s": create_s},
          "roofline_graph": {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                             "frac": achieved / tc_peak, "issued_frac": issued / (per_launch_ms / 1e3) / 1e12 / tc_peak,

@@ -311,10 +311,13 @@ FV_API int fv_gmm_fit(const fv_gmm_desc *init, const float *X, int64_t N, int x_
  * frame; the per-block copies and reduction of Algorithm 3 become per-share
  * statistics slots reduced per frame). FV_PREC_BF16 handles only.
  *
- * The statistics grid is chosen by a measured autotune at creation (when
- * requested): candidate grids are timed on a synthetic batch of the plan's
- * capacity, the fastest is kept and written to tune_cache (one line per
- * GPU model, SM count, K, D and capacity), which later plans read back. */
+ * The tile pipeline is chosen by a measured autotune at creation (when
+ * requested): every pair of Y-stage count (1, or 2 where two fit shared
+ * memory) and share count (1, 2, 3 and 4 times the clusters resident at
+ * once; the share count sets the tiles per share) is timed on a synthetic
+ * batch of the plan's capacity; the fastest pair is kept and written to
+ * tune_cache (one line per GPU model, SM count, K, D, capacity and
+ * precision), which later plans read back. Rows per tile are the MMA's M. */
 typedef struct fv_batch_plan fv_batch_plan;
 
 typedef struct {
@@ -325,12 +328,16 @@ typedef struct {
 } fv_batch_plan_config;
 
 typedef struct {
-    int stat_ctas;           /* statistics CTAs per component group (row shares) */
+    int stat_ctas;           /* persistent clusters = row shares of a batch */
     int tuned;               /* 1: chosen by timing now, 2: read from tune_cache, 0: default */
     double tuned_ms;         /* best candidate's time (ms) when tuned now */
     int64_t max_rows;
     int max_frames;
     int ld_x;                /* row pitch (elements) of the plan's input buffer */
+    int rows_per_tile;       /* M of the log-likelihood MMA (128) */
+    int y_stages;            /* tiles whose [X | X^2 | 1] planes are in flight per CTA (1 or 2) */
+    int candidates;          /* (stages, shares) pairs timed by the autotune */
+    double tiles_per_share;  /* at the plan's capacity */
 } fv_batch_plan_info;
 
 FV_API int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_config *cfg, fv_batch_plan **out);

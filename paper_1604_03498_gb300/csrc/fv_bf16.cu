@@ -843,13 +843,22 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
     return cudaGetLastError();
 }
 
+int bf16_max_stages(const fv_gmm *g) {
+    EncCfg c;
+    return enc_config(g, c) ? c.nstage : 1;
+}
+
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, const StatUnit *units,
                      const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st,
-                     float tau, unsigned long long *skip_count) {
+                     float tau, unsigned long long *skip_count, int nstage) {
     if (rows <= 0 || n_shares <= 0) return FV_OK;
     if (get_encoder() != cudaSuccess) return fail(FV_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
     EncCfg c;
     if (!enc_config(g, c)) return fail(FV_ERR_UNSUPPORTED, "BF16 form: shape does not fit the kernel's shared memory");
+    if (nstage > 0 && nstage < c.nstage) {   // fewer stages than fit (the autotuner's choice)
+        c.nstage = nstage;
+        c.smem = enc_smem(c.nkb, c.S, c.nstage, c.glo).total;
+    }
     if (P != 3 * c.nkb * 16 + 1) return fail(FV_ERR_INVALID, "BF16 form: slot width mismatch");
     if (rows > (int64_t)INT32_MAX - 256) return fail(FV_ERR_UNSUPPORTED, "BF16 form: too many rows for one call");
 

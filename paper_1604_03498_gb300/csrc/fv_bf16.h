@@ -23,8 +23,13 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
 // tau > 0: early termination (posteriors <= tau dropped, all-zero 16-row
 // K steps of the statistics GEMM skipped); skip_count (device, nullable):
 // [skipped, visited] K steps.
+// nstage: Y-plane stages of the tile pipeline (0 = the most that fit shared
+// memory; 1 or 2 to choose, e.g. by the batched form's autotuner).
 int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t rows, const StatUnit *units,
                      const int2 *cl_units, int n_shares, float *part, int P, uint32_t *err, cudaStream_t st,
-                     float tau = 0.f, unsigned long long *skip_count = nullptr);
+                     float tau = 0.f, unsigned long long *skip_count = nullptr, int nstage = 0);
+
+// Y-plane stages that fit shared memory for this GMM (1 or 2).
+int bf16_max_stages(const fv_gmm *g);
 
 }  // namespace fv

@@ -53,25 +53,32 @@ std::string gpu_key(int dev, int sms, const fv_gmm *g, int64_t max_rows, int max
     for (auto &ch : name)
         if (ch == ' ' || ch == '|') ch = '_';
     std::ostringstream os;
-    os << name << "|" << sms << "|" << g->K << "|" << g->D << "|" << max_rows << "|" << max_frames;
+    os << name << "|" << sms << "|" << g->K << "|" << g->D << "|" << max_rows << "|" << max_frames << "|p" << g->prec;
     return os.str();
 }
 
-int read_cache(const char *path, const std::string &key) {
-    if (!path) return 0;
+// Cache lines: key|G|stages (later lines win).
+bool read_cache(const char *path, const std::string &key, int *G, int *stages) {
+    if (!path) return false;
     std::ifstream f(path);
-    std::string line, best;
+    std::string line;
+    bool found = false;
     while (std::getline(f, line)) {
-        const size_t eq = line.rfind('|');
-        if (eq != std::string::npos && line.compare(0, eq, key) == 0) best = line.substr(eq + 1);
+        if (line.compare(0, key.size(), key) != 0 || line.size() <= key.size() || line[key.size()] != '|') continue;
+        int g = 0, st = 0;
+        if (std::sscanf(line.c_str() + key.size() + 1, "%d|%d", &g, &st) == 2 && g > 0 && st > 0) {
+            *G = g;
+            *stages = st;
+            found = true;
+        }
     }
-    return best.empty() ? 0 : std::atoi(best.c_str());
+    return found;
 }
 
-void write_cache(const char *path, const std::string &key, int G) {
+void write_cache(const char *path, const std::string &key, int G, int stages) {
     if (!path) return;
     std::ofstream f(path, std::ios::app);
-    f << key << "|" << G << "\n";
+    f << key << "|" << G << "|" << stages << "\n";
 }
 
 }  // namespace
@@ -82,6 +89,7 @@ using namespace fv;
 struct fv_batch_plan {
     const fv_gmm *g = nullptr;
     int device = 0, sms = 1, base = 1, G = 1, Gmax = 1, P = 0, max_frames = 0, max_units = 0;
+    int nstage = 0;   // Y stages of the encoder (0: the most that fit)
     int64_t max_rows = 0;
     fv_batch_plan_info info{};
     char *block = nullptr;
@@ -131,7 +139,8 @@ int launch_sequence(fv_batch_plan *p, int G, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "batch plan: error word");
     const int *B_dev = (const int *)(p->wl + 8);
     int rc = run_bf16_encoder(g, p->xin, g->Dp, p->max_rows, (const StatUnit *)(p->wl + p->off_units),
-                              (const int2 *)(p->wl + p->off_cta), G, p->part, p->P, p->err, st);
+                              (const int2 *)(p->wl + p->off_cta), G, p->part, p->P, p->err, st, 0.f, nullptr,
+                              p->nstage);
     if (rc != FV_OK) return rc;
     if ((e = launch_finalize(g, p->part, p->P, true, (const FrameInfo *)(p->wl + p->off_frames), p->max_frames, p->sq,
                              p->out, st, p->err, B_dev)) != cudaSuccess)
@@ -154,38 +163,42 @@ int autotune(fv_batch_plan *p, cudaStream_t st, double *best_ms) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     const int base = p->base;
-    int bestG = base;
+    int bestG = base, bestS = bf16_max_stages(p->g);
     *best_ms = 1e30;
-    for (int f = 1; f <= 3; ++f) {
-        const int G = std::min(p->Gmax, base * f);
-        float best = 1e30f;
-        int rc = upload_work(p, offs.data(), B, G, st);
-        for (int it = 0; rc == FV_OK && it < 5; ++it) {
-            cudaEventRecord(a, st);
-            rc = launch_sequence(p, G, st);
-            cudaEventRecord(b, st);
-            if (rc == FV_OK && cudaEventSynchronize(b) == cudaSuccess && it >= 2) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, a, b);
-                best = std::min(best, ms);
+    int rc = FV_OK, cands = 0;
+    for (int stages = bf16_max_stages(p->g); rc == FV_OK && stages >= 1; --stages) {
+        for (int f = 1; rc == FV_OK && f <= 4; ++f) {
+            const int G = std::min(p->Gmax, base * f);
+            p->nstage = stages;
+            float best = 1e30f;
+            rc = upload_work(p, offs.data(), B, G, st);
+            for (int it = 0; rc == FV_OK && it < 5; ++it) {
+                cudaEventRecord(a, st);
+                rc = launch_sequence(p, G, st);
+                cudaEventRecord(b, st);
+                if (rc == FV_OK && cudaEventSynchronize(b) == cudaSuccess && it >= 2) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, a, b);
+                    best = std::min(best, ms);
+                }
             }
-        }
-        if (rc != FV_OK) {
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
-            return rc;
-        }
-        if (best < *best_ms) {
-            *best_ms = best;
-            bestG = G;
+            ++cands;
+            if (rc == FV_OK && best < *best_ms) {
+                *best_ms = best;
+                bestG = G;
+                bestS = stages;
+            }
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    if (rc != FV_OK) return rc;
     uint32_t errh = 0;
     cudaMemcpy(&errh, p->err, sizeof(errh), cudaMemcpyDeviceToHost);
     if (errh) return fail(FV_ERR_DEVICE, "batch plan: a kernel gave up during the autotune");
     p->G = bestG;
+    p->nstage = bestS;
+    p->info.candidates = cands;
     return FV_OK;
 }
 
@@ -226,7 +239,8 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
     p->max_frames = cfg->max_frames;
     p->max_rows = cfg->max_rows;
     p->P = 3 * gmm->Dp + 1;
-    p->Gmax = 3 * p->base;
+    p->Gmax = 4 * p->base;
+    p->nstage = bf16_max_stages(gmm);
     p->G = p->base;
     p->max_units = p->Gmax + p->max_frames;
 
@@ -276,17 +290,18 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
             break;
         }
         const std::string key = gpu_key(dev, p->sms, gmm, p->max_rows, p->max_frames);
-        const int cached = read_cache(cfg->tune_cache, key);
+        int cG = 0, cS = 0;
         p->info.tuned = 0;
-        if (cached > 0 && cached <= p->Gmax) {
-            p->G = cached;
+        if (read_cache(cfg->tune_cache, key, &cG, &cS) && cG <= p->Gmax && cS <= bf16_max_stages(gmm)) {
+            p->G = cG;
+            p->nstage = cS;
             p->info.tuned = 2;
         } else if (cfg->autotune) {
             double ms = 0.0;
             if ((rc = autotune(p, st, &ms)) != FV_OK) break;
             p->info.tuned = 1;
             p->info.tuned_ms = ms;
-            write_cache(cfg->tune_cache, key, p->G);
+            write_cache(cfg->tune_cache, key, p->G, p->nstage);
             cudaMemsetAsync(p->xin, 0, sizeof(uint16_t) * (size_t)p->max_rows * Dp, st);
         }
         // capture the kernel sequence once
@@ -326,6 +341,9 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
     p->info.max_rows = p->max_rows;
     p->info.max_frames = p->max_frames;
     p->info.ld_x = gmm->Dp;
+    p->info.rows_per_tile = 128;
+    p->info.y_stages = p->nstage;
+    p->info.tiles_per_share = (double)((p->max_rows + 127) / 128) / p->G;
     *out = p;
     return FV_OK;
 }

@@ -65,7 +65,9 @@ class fv_batch_plan_config(ctypes.Structure):
 
 class fv_batch_plan_info(ctypes.Structure):
     _fields_ = [("stat_ctas", ctypes.c_int), ("tuned", ctypes.c_int), ("tuned_ms", ctypes.c_double),
-                ("max_rows", ctypes.c_int64), ("max_frames", ctypes.c_int), ("ld_x", ctypes.c_int)]
+                ("max_rows", ctypes.c_int64), ("max_frames", ctypes.c_int), ("ld_x", ctypes.c_int),
+                ("rows_per_tile", ctypes.c_int), ("y_stages", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("tiles_per_share", ctypes.c_double)]
 
 
 class fv_server_config(ctypes.Structure):
