@@ -4,10 +4,10 @@
 //   l_ik = c'_k - 1/2 sum_d t_ikd^2,  t_ikd = x_id/sigma_kd - mu_kd/sigma_kd
 //   gamma_ik = exp(l_ik - max_k l_ik) / sum_k exp(l_ik - max_k l_ik)
 // (evaluated in base 2 on y = l log2(e))
-// computed for a 64-row block against every component with register tiles of
-// 8 rows x CPL components per thread (t is one FMA, t^2 accumulation another,
-// both on component pairs with packed f32x2 instructions),
-// the row block's log-likelihoods kept in shared memory for the softmax.
+// computed for 4 rows per warp against every component, a lane holding
+// CPL components of each 32 CPL-component chunk (t is one FMA, t^2
+// accumulation another, both on component pairs with packed f32x2
+// instructions); the log-likelihoods stay in registers for the softmax.
 //
 // Statistics (Algorithm 1 second loop; the paper's Phase 2, Algorithm 3 with
 // one private copy of U, V per block): each block owns one row range and one
@@ -84,48 +84,48 @@ __device__ __forceinline__ float ex2f_approx(float x) {
     return y;
 }
 
-constexpr int P_BM = 64;   // rows per posterior block
-constexpr int P_DS = 16;   // dimension slice staged in shared memory
 constexpr int P_THREADS = 256;
 
-// Dynamic shared memory layout of the posteriors kernel:
-//   two stages of
-//     sS[P_DS][KC], sN[P_DS][KC]   1/sigma and -mu/sigma of a (component chunk, dimension slice)
-//     sX[P_DS][P_BM + 4]           descriptor slice, dimension-major
-//   sL[P_BM][Kp]                   log-likelihoods of the row block
-// The (chunk, slice) phases run in order; phase p + 1 is copied in by
-// cp.async while phase p is computed.
-template <int CPL>
-__global__ void __launch_bounds__(P_THREADS)
-f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
-                      const float *__restrict__ s_t, const float *__restrict__ nms_t,
-                      const float *__restrict__ cst, float *__restrict__ gamma, float *__restrict__ lse) {
-    constexpr int KC = 32 * CPL;
-    constexpr int XS = P_BM + 4;
-    constexpr int STAGE = 2 * P_DS * KC + P_DS * XS;
+// Posteriors kernel: a warp owns 4 rows and every component (lane l holds
+// components c KCH + l CPL .. + CPL - 1 of each chunk c of KCH = 32 CPL), so a
+// row's log-likelihoods never leave registers and the row softmax is a pair
+// of warp shuffle reductions. The block (8 warps, 32 rows) stages only the
+// GMM slices and the descriptor slice, 8 dimensions at a time (double-buffered
+// by cp.async), so three blocks fit an SM at K <= 256 (a version that kept a
+// 64 x Kp log-likelihood block in shared memory fitted two and ran 10-17%
+// slower).
+constexpr int R_ROWS = 4;              // rows per warp
+constexpr int R_BM = 8 * R_ROWS;       // rows per block
+constexpr int R_DS = 8;                // dimension slice
+
+template <int CPL, int NC>
+__global__ void __launch_bounds__(P_THREADS, (CPL * NC <= 8) ? 3 : 2)
+f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, const float *__restrict__ s_t,
+                    const float *__restrict__ nms_t, const float *__restrict__ cst, float *__restrict__ gamma,
+                    float *__restrict__ lse) {
+    constexpr int KCH = 32 * CPL;          // components per chunk
+    constexpr int KT = KCH * NC;           // all (padded) components
+    constexpr int XS = R_BM + 4;
+    constexpr int STAGE = 2 * R_DS * KT + R_DS * XS;
     extern __shared__ __align__(16) float smem[];
-    float *sL = smem + 2 * STAGE;
 
     pdl_trigger();   // the statistics kernel may start launching (it waits for this grid)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * P_BM;
-    const int nslice = (D + P_DS - 1) / P_DS, nphase = (Kp / KC) * nslice;
+    const int64_t row0 = (int64_t)blockIdx.x * R_BM;
+    const int nslice = (D + R_DS - 1) / R_DS;
 
-    auto issue = [&](int ph, int b) {
-        const int kc0 = (ph / nslice) * KC, d0 = (ph % nslice) * P_DS;
-        float *bS = smem + b * STAGE, *bN = bS + P_DS * KC, *bX = bN + P_DS * KC;
+    auto issue = [&](int sl, int b) {
+        const int d0 = sl * R_DS;
+        float *bS = smem + b * STAGE, *bN = bS + R_DS * KT, *bX = bN + R_DS * KT;
 #pragma unroll
-        for (int q = 0; q < P_DS * KC / 4 / P_THREADS; ++q) {   // 16-byte chunks of the GMM slices
-            const int i = tid + q * P_THREADS;
-            const int dd = i / (KC / 4), c4 = (i % (KC / 4)) * 4, d = d0 + dd;
+        for (int i = tid; i < R_DS * KT / 4; i += P_THREADS) {   // 16-byte chunks of the GMM slices
+            const int dd = i / (KT / 4), c4 = (i % (KT / 4)) * 4, d = d0 + dd;
             const bool ok = d < D;
-            cp_async<16>(bS + dd * KC + c4, ok ? s_t + (size_t)d * Kp + kc0 + c4 : s_t, ok);
-            cp_async<16>(bN + dd * KC + c4, ok ? nms_t + (size_t)d * Kp + kc0 + c4 : nms_t, ok);
+            cp_async<16>(bS + dd * KT + c4, ok ? s_t + (size_t)d * Kp + c4 : s_t, ok);
+            cp_async<16>(bN + dd * KT + c4, ok ? nms_t + (size_t)d * Kp + c4 : nms_t, ok);
         }
-#pragma unroll
-        for (int q = 0; q < P_DS * P_BM / P_THREADS; ++q) {     // descriptors, transposed
-            const int i = tid + q * P_THREADS;
-            const int r = i / P_DS, dd = i % P_DS, d = d0 + dd;
+        {   // the block's descriptor slice, dimension-major (R_BM * R_DS == P_THREADS)
+            const int r = tid / R_DS, dd = tid % R_DS, d = d0 + dd;
             const int64_t row = row0 + r;
             const bool ok = row < rows && d < D;
             cp_async<4>(bX + dd * XS + r, ok ? X + row * D + d : X, ok);
@@ -134,108 +134,100 @@ f32_posteriors_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp,
     };
     issue(0, 0);
 
-    uint64_t acc[8][CPL / 2];   // component pairs
+    uint64_t acc[R_ROWS][NC][CPL / 2];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < R_ROWS; ++r)
 #pragma unroll
-        for (int c = 0; c < CPL / 2; ++c) acc[r][c] = 0ull;
-    for (int ph = 0; ph < nphase; ++ph) {
-        const int b = ph & 1;
-        if (ph + 1 < nphase) issue(ph + 1, b ^ 1);
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int p = 0; p < CPL / 2; ++p) acc[r][c][p] = 0ull;
+
+    for (int sl = 0; sl < nslice; ++sl) {
+        const int b = sl & 1;
+        if (sl + 1 < nslice) issue(sl + 1, b ^ 1);
         else cp_async_commit();   // an empty group keeps the wait count uniform
-        cp_async_wait1();         // this phase's copies (of this thread) have landed
-        __syncthreads();          // ... and every thread's
-        const float *sS = smem + b * STAGE, *sN = sS + P_DS * KC, *sX = sN + P_DS * KC;
-        // the shared-memory operands of slice dd + 1 are loaded into
-        // registers while slice dd is computed (the loads' latency is hidden)
-        float4 pxa, pxb;
-        float pv[2 * CPL];   // CPL scale values, then CPL offsets
-        auto load = [&](int dd) {
-            pxa = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8]);
-            pxb = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * 8 + 4]);
-            if constexpr (CPL == 4) {
-                const float4 a = *reinterpret_cast<const float4 *>(&sS[dd * KC + lane * 4]);
-                const float4 c = *reinterpret_cast<const float4 *>(&sN[dd * KC + lane * 4]);
-                pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
-                pv[4] = c.x; pv[5] = c.y; pv[6] = c.z; pv[7] = c.w;
-            } else {
-                const float2 a = *reinterpret_cast<const float2 *>(&sS[dd * KC + lane * 2]);
-                const float2 c = *reinterpret_cast<const float2 *>(&sN[dd * KC + lane * 2]);
-                pv[0] = a.x; pv[1] = a.y;
-                pv[2] = c.x; pv[3] = c.y;
-            }
-        };
-        load(0);
+        cp_async_wait1();
+        __syncthreads();
+        const float *sS = smem + b * STAGE, *sN = sS + R_DS * KT, *sX = sN + R_DS * KT;
 #pragma unroll
-        for (int dd = 0; dd < P_DS; ++dd) {
-            const float xv[8] = {pxa.x, pxa.y, pxa.z, pxa.w, pxb.x, pxb.y, pxb.z, pxb.w};
-            uint64_t s2[CPL / 2], n2[CPL / 2];
+        for (int dd = 0; dd < R_DS; ++dd) {
+            const float4 xv = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * R_ROWS]);
+            const uint64_t x2[R_ROWS] = {pk2(xv.x, xv.x), pk2(xv.y, xv.y), pk2(xv.z, xv.z), pk2(xv.w, xv.w)};
 #pragma unroll
-            for (int c = 0; c < CPL / 2; ++c) {
-                s2[c] = pk2(pv[2 * c], pv[2 * c + 1]);
-                n2[c] = pk2(pv[CPL + 2 * c], pv[CPL + 2 * c + 1]);
-            }
-            if (dd + 1 < P_DS) load(dd + 1);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const uint64_t x2 = pk2(xv[r], xv[r]);
-#pragma unroll
-                for (int c = 0; c < CPL / 2; ++c) {
-                    const uint64_t t = fma2(x2, s2[c], n2[c]);
-                    acc[r][c] = fma2(t, t, acc[r][c]);
+            for (int c = 0; c < NC; ++c) {
+                uint64_t s2[CPL / 2], n2[CPL / 2];
+                const int k = c * KCH + lane * CPL;
+                if constexpr (CPL == 4) {
+                    const float4 a = *reinterpret_cast<const float4 *>(&sS[dd * KT + k]);
+                    const float4 o = *reinterpret_cast<const float4 *>(&sN[dd * KT + k]);
+                    s2[0] = pk2(a.x, a.y);
+                    s2[1] = pk2(a.z, a.w);
+                    n2[0] = pk2(o.x, o.y);
+                    n2[1] = pk2(o.z, o.w);
+                } else {
+                    const float2 a = *reinterpret_cast<const float2 *>(&sS[dd * KT + k]);
+                    const float2 o = *reinterpret_cast<const float2 *>(&sN[dd * KT + k]);
+                    s2[0] = pk2(a.x, a.y);
+                    n2[0] = pk2(o.x, o.y);
                 }
+#pragma unroll
+                for (int r = 0; r < R_ROWS; ++r)
+#pragma unroll
+                    for (int p = 0; p < CPL / 2; ++p) {
+                        const uint64_t t = fma2(x2[r], s2[p], n2[p]);
+                        acc[r][c][p] = fma2(t, t, acc[r][c][p]);
+                    }
             }
         }
-        if (ph % nslice == nslice - 1) {   // chunk done: y = (c' - dist/2) log2(e)
-            const int kc0 = (ph / nslice) * KC;
-#pragma unroll
-            for (int c = 0; c < CPL / 2; ++c) {
-                const float ck0 = cst[kc0 + lane * CPL + 2 * c] * kLog2eF, ck1 = cst[kc0 + lane * CPL + 2 * c + 1] * kLog2eF;
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    float a0, a1;
-                    up2(acc[r][c], a0, a1);
-                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c] = fmaf(-0.5f * kLog2eF, a0, ck0);
-                    sL[(warp * 8 + r) * Kp + kc0 + lane * CPL + 2 * c + 1] = fmaf(-0.5f * kLog2eF, a1, ck1);
-                    acc[r][c] = 0ull;
-                }
-            }
-        }
-        __syncthreads();   // the stage is consumed before it is refilled (and sL is complete at the end)
+        __syncthreads();   // the stage is consumed before it is refilled
     }
 
-    // row softmax in base 2: each warp owns its 8 rows, a lane holds up to 16
-    // of a row's values in registers (Kp <= 512)
-    for (int r = 0; r < 8; ++r) {
-        const int lr = warp * 8 + r;
-        const int64_t row = row0 + lr;
-        if (row >= rows) break;
-        const float *L = sL + (size_t)lr * Kp;
-        const int nk = Kp >> 5;
-        float v[16];
+    // y = (c' - dist/2) log2(e), row softmax in base 2 across the warp
+    float cl[NC][CPL];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) cl[c][j] = cst[c * KCH + lane * CPL + j] * kLog2eF;
+#pragma unroll
+    for (int r = 0; r < R_ROWS; ++r) {
+        const int64_t row = row0 + warp * R_ROWS + r;
+        float y[NC][CPL];
         float m = -INFINITY;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            v[j] = j < nk ? L[lane + 32 * j] : -INFINITY;
-            m = fmaxf(m, v[j]);
-        }
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int p = 0; p < CPL / 2; ++p) {
+                float a0, a1;
+                up2(acc[r][c][p], a0, a1);
+                y[c][2 * p] = fmaf(-0.5f * kLog2eF, a0, cl[c][2 * p]);
+                y[c][2 * p + 1] = fmaf(-0.5f * kLog2eF, a1, cl[c][2 * p + 1]);
+                m = fmaxf(m, fmaxf(y[c][2 * p], y[c][2 * p + 1]));
+            }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         float z = 0.f;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            v[j] = j < nk ? ex2f_approx(v[j] - m) : 0.f;
-            z += v[j];
-        }
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                y[c][j] = ex2f_approx(y[c][j] - m);
+                z += y[c][j];
+            }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (row >= rows) continue;
         // the row's log-sum-exp, log sum_k exp(l_ik) = ln 2 (m + log2 z) (natural log; EM's log-likelihood)
         if (lse && lane == 0) lse[row] = (m + log2f(z)) * 0.69314718055994531f;
         const float iz = 1.0f / z;
         float *G = gamma + row * Kp;
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (j < nk) G[lane + 32 * j] = v[j] * iz;
+        for (int c = 0; c < NC; ++c) {
+            if constexpr (CPL == 4)
+                *reinterpret_cast<float4 *>(G + c * KCH + lane * 4) =
+                    make_float4(y[c][0] * iz, y[c][1] * iz, y[c][2] * iz, y[c][3] * iz);
+            else
+                *reinterpret_cast<float2 *>(G + c * KCH + lane * 2) = make_float2(y[c][0] * iz, y[c][1] * iz);
+        }
     }
 }
 
@@ -405,33 +397,37 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
 
 }  // namespace
 
+namespace {
+template <int CPL, int NC>
+cudaError_t launch_post_reg(const fv_gmm *g, const float *X, int64_t rows, float *gamma, cudaStream_t st, float *lse) {
+    constexpr int KT = 32 * CPL * NC;
+    const size_t smem = sizeof(float) * 2 * (2 * R_DS * KT + R_DS * (R_BM + 4));
+    cudaError_t e = cudaFuncSetAttribute(f32_post_reg_kernel<CPL, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    {
+        KernelTimer kt_("f32_posteriors", st);
+        f32_post_reg_kernel<CPL, NC><<<(unsigned)((rows + R_BM - 1) / R_BM), P_THREADS, smem, st>>>(
+            X, rows, g->D, g->Kp, g->dev.s_t, g->dev.nms_t, g->dev.cst, gamma, lse);
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma, cudaStream_t st,
                                   float *lse) {
     if (rows <= 0) return cudaSuccess;
-    const int Kp = g->Kp;
-    const int cpl = (Kp % 128 == 0) ? 4 : 2;
-    const int KC = 32 * cpl;
-    const size_t smem = sizeof(float) * (2 * (2 * P_DS * KC + P_DS * (P_BM + 4)) + (size_t)P_BM * Kp);
-    const unsigned grid = (unsigned)((rows + P_BM - 1) / P_BM);
-    cudaError_t e;
-    if (cpl == 4) {
-        e = cudaFuncSetAttribute(f32_posteriors_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        {
-        KernelTimer kt_("f32_posteriors", st);
-        f32_posteriors_kernel<4><<<grid, P_THREADS, smem, st>>>(X, rows, g->D, Kp, g->dev.s_t, g->dev.nms_t,
-                                                                g->dev.cst, gamma, lse);
+    switch (g->Kp) {   // Kp is K rounded up to 64, at most 512
+        case 64: return launch_post_reg<2, 1>(g, X, rows, gamma, st, lse);
+        case 128: return launch_post_reg<4, 1>(g, X, rows, gamma, st, lse);
+        case 192: return launch_post_reg<2, 3>(g, X, rows, gamma, st, lse);
+        case 256: return launch_post_reg<4, 2>(g, X, rows, gamma, st, lse);
+        case 320: return launch_post_reg<2, 5>(g, X, rows, gamma, st, lse);
+        case 384: return launch_post_reg<4, 3>(g, X, rows, gamma, st, lse);
+        case 448: return launch_post_reg<2, 7>(g, X, rows, gamma, st, lse);
+        case 512: return launch_post_reg<4, 4>(g, X, rows, gamma, st, lse);
+        default: return cudaErrorInvalidValue;
     }
-    } else {
-        e = cudaFuncSetAttribute(f32_posteriors_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        {
-        KernelTimer kt_("f32_posteriors", st);
-        f32_posteriors_kernel<2><<<grid, P_THREADS, smem, st>>>(X, rows, g->D, Kp, g->dev.s_t, g->dev.nms_t,
-                                                                g->dev.cst, gamma, lse);
-    }
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
