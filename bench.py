@@ -729,6 +729,8 @@ def ncu_case(kind: str) -> int:
     frames (157 MB of bf16 descriptors, larger than L2) in one call."""
     import torch
     from paper_1604_03498_gb300 import fv
+    if kind in ("pca", "images"):
+        return ncu_case_pipeline(kind)
     w, mu, var, frames = make_pool(0, 64 if kind == "bf16_batched" else 16)
     X = torch.from_numpy(np.stack(frames)).cuda()
     KD = K_COMP * D_DIM
@@ -751,6 +753,37 @@ def ncu_case(kind: str) -> int:
     torch.cuda.synchronize()
     g.close()
     print("ncu case", kind, "done, fv norm", float(out[0].norm()))
+    return 0
+
+
+def ncu_case_pipeline(kind: str) -> int:
+    """pca: 16 frames of 19200 raw 128-d descriptors (157 MB FP32, larger than L2) through
+    fv_encode_pca in the BF16 form, one frame per call, twice; images: 16 320x240 frames
+    through fv_encode_images (dense SIFT, PCA, BF16 encoder), 8 frames per call, twice."""
+    import torch
+    from paper_1604_03498_gb300 import fv
+    m, K = 62, 256
+    P, mean = synth.make_pca(128, m, seed=7)
+    w, mu, var = synth.make_gmm(K, m + 2, seed=7)
+    g = fv.fv_gmm_load(w, 0.3 * mu, 0.05 * var, fv.FV_PREC_BF16)
+    pca = fv.fv_pca_load(P, mean)
+    if kind == "pca":
+        X = torch.from_numpy(np.stack([synth.sample_sift_like(N_DESC, 128, seed=700 + f) for f in range(16)])).cuda()
+        xy = torch.from_numpy(np.stack([synth.sample_positions(N_DESC, seed=700 + f) for f in range(16)])).cuda()
+        out = torch.zeros(16, 2 * K * (m + 2), device="cuda")
+        for _ in range(2):
+            for f in range(16):
+                fv.fv_encode_pca(g, pca, X[f], xy[f], [0, N_DESC], out[f:f + 1], allow=(fv.FV_OK,))
+    else:
+        frames = torch.from_numpy(synth.make_frames(16, 240, 320, seed=11)).cuda()
+        out = torch.zeros(16, 2 * K * (m + 2), device="cuda")
+        for _ in range(2):
+            for c in range(2):
+                fv.fv_encode_images(g, pca, frames[8 * c:8 * c + 8], out[8 * c:8 * c + 8])
+    torch.cuda.synchronize()
+    print("ncu case", kind, "done, fv norm", float(out[0].norm()))
+    g.close()
+    pca.close()
     return 0
 
 
@@ -809,7 +842,7 @@ def main():
                          "shorter for quick runs)")
     ap.add_argument("--config", choices=["c1", "c3"], default=None,
                     help="time one of the other workload shapes alone and exit (not the headline)")
-    ap.add_argument("--ncu-case", choices=["fp32", "bf16", "bf16_batched"], default=None,
+    ap.add_argument("--ncu-case", choices=["fp32", "bf16", "bf16_batched", "pca", "images"], default=None,
                     help="run a small fixed workload twice and exit (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
