@@ -264,7 +264,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     const size_t o_x = (!x_on_device && rows > 0) ? s.take(sizeof(float) * rows * D) : 0;
     const bool need_x_f32_stage = !x_on_device && rows > 0;
     const size_t o_xb = (bf16 && !x_bf16 && rows > 0) ? s.take(sizeof(uint16_t) * rows * ldx_dev) : 0;
-    const size_t o_gam = !bf16 ? s.take(sizeof(float) * std::max<int64_t>(rows, 1) * Kp) : 0;
+    const size_t o_gam = !bf16 ? s.take(f32_gamma_bytes(std::max<int64_t>(rows, 1), Kp)) : 0;
     const size_t o_part = s.take(sizeof(float) * std::max(nslots, 1) * (size_t)Kp * P);
     // the work list (frames, units, shares) and the zeroed error word go up
     // in one staged copy
@@ -316,7 +316,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
                 rc = cuda_fail(e, "f32 posteriors launch");
                 break;
             }
-            if ((e = launch_f32_stats(g, (const float *)Xd, gam, und, nslots, part, P, st, true, tau, skip_count)) !=
+            if ((e = launch_f32_stats(g, (const float *)Xd, gam, rows, und, nslots, part, P, st, true, tau, skip_count)) !=
                 cudaSuccess) {
                 rc = cuda_fail(e, "f32 statistics launch");
                 break;

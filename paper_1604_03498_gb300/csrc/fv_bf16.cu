@@ -487,10 +487,11 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         // (their TMEM lane quadrant), one row per thread, over components
         // 64h..64h+63 (h = 0 for warps 4-7, 1 for 8-11) in two 32-column
         // chunks. Pass A forms y = l log2(e) + c log2(e), keeps an online row
-        // max/sum with a reference max per chunk and stores 2^(y - ref) back
-        // into TMEM; the two halves of a row combine their (max, sum) through
-        // shared memory, then the cluster's CTAs combine theirs; pass B
-        // rescales each chunk and writes bf16 gamma^T to shared memory. After
+        // max/sum with a reference max per chunk and holds 2^(y - ref) in
+        // registers (the TMEM buffer is released at once); the two halves of a
+        // row combine their (max, sum) through shared memory, then the
+        // cluster's CTAs combine theirs; pass B rescales each chunk and writes
+        // bf16 gamma^T to shared memory. After
         // a unit's last tile the eight warps write the unit's statistics from
         // TMEM to its slot (half the columns each).
         const int h = (warp - 4) >> 2, q = warp & 3;
@@ -559,11 +560,14 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                     cur[k + 3] = __float_as_uint(e3);
                 }
                 z = (z0 + z1) + (z2 + z3);
-                tmem_st32_nowait(ta + c * 32, cur);
                 mc[c] = mref;
                 m = mn;
             }
-            tmem_st_wait();   // the exponentials are in TMEM before pass B reads them back
+            // the exponentials stay in registers (ra, rb) for pass B, so this
+            // tile's log-likelihood buffer is free for the GEMM of tile i + 2
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars[EB_LEMPTY + b]);
             // the row's two halves: (max, sum) of both, combined in half order
             // (bounded handshakes: the partner has read the previous tile's
             // value before this one is written, and written this tile's before
@@ -631,14 +635,11 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             // warps wait on every phase of GFREE in order, so none is skipped)
             if (i >= 1 &&
                 !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], (i - 1) & 1, abort_flag, p.err))) break;
-            // pass B: normalised posteriors -> bf16 gamma^T (second chunk's load in flight)
-            tmem_ld32_issue(ta, ra);
-            tmem_ld_wait(ra);
+            // pass B: normalised posteriors -> bf16 gamma^T from the registers of pass A
             bool row_nz = false;   // early termination: a posterior of this row and half above tau
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 uint32_t(&cur)[32] = c ? rb : ra;
-                if (c == 0) tmem_ld32_issue(ta + 32, rb);
                 const float sc = ex2_approx(mc[c] - Mref) * inv;
                 if constexpr (SPARSE) {   // posteriors not above tau are dropped
                     const float tau = p.tau;
@@ -674,7 +675,6 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                         *reinterpret_cast<uint4 *>(gsm + (((c * 4 + k) ^ sw) << 4)) = v;
                     }
                 }
-                if (c == 0) tmem_ld_wait(rb);
             }
             if constexpr (SPARSE) {   // marks of this warp's two 16-row K steps (its half of the components)
                 const uint32_t bal = __ballot_sync(0xffffffffu, row_nz);
@@ -684,12 +684,8 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                 }
             }
             fence_proxy_async_smem();
-            tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&bars[EB_GFULL]);
-                mbar_arrive(&bars[EB_LEMPTY + b]);
-            }
+            if (lane == 0) mbar_arrive(&bars[EB_GFULL]);
             const bool last = w.last();
             const int uidx = w.ui, uslot = w.slot();
             w.next();

@@ -95,7 +95,7 @@ int em_scratch(const fv_gmm *g, int64_t N, cudaStream_t st, EmScratch &s) {
         units[u].slot = u;
     }
     FrameInfo fr{0, N, 0, s.nunits};
-    const size_t b_gam = al256(sizeof(float) * N * Kp), b_lse = al256(sizeof(float) * N);
+    const size_t b_gam = al256(f32_gamma_bytes(N, Kp)), b_lse = al256(sizeof(float) * N);
     const size_t b_part = al256(sizeof(float) * (size_t)s.nunits * Kp * s.P);
     const size_t b_fr = al256(sizeof(FrameInfo)), b_un = al256(sizeof(StatUnit) * s.nunits), b_ll = al256(8);
     cudaError_t e = cudaMallocAsync((void **)&s.base, b_gam + b_lse + b_part + b_fr + b_un + b_ll, st);
@@ -126,7 +126,7 @@ int em_step_device(const fv_gmm *g, const float *Xd, int64_t N, double reg, floa
     cudaError_t e;
     if ((e = launch_f32_posteriors(g, Xd, N, s.gam, st, s.lse)) != cudaSuccess)
         return cuda_fail(e, "EM: posteriors launch");
-    if ((e = launch_f32_stats(g, Xd, s.gam, s.units, s.nunits, s.part, s.P, st)) != cudaSuccess)
+    if ((e = launch_f32_stats(g, Xd, s.gam, N, s.units, s.nunits, s.part, s.P, st)) != cudaSuccess)
         return cuda_fail(e, "EM: statistics launch");
     if ((e = launch_slot_reduce(g, s.part, s.P, s.frame, 1, s.nunits, st)) != cudaSuccess)
         return cuda_fail(e, "EM: slot reduction launch");

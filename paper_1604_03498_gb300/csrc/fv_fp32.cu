@@ -22,7 +22,11 @@
 // exactly zero (the FP32 exponential underflows for every component far from
 // the descriptor, most of them in 64 dimensions) add exact zeros, so a warp
 // skips a row when all its components' posteriors are zero: the sums are
-// bitwise those of the dense loop. Every block writes its own statistics slot;
+// bitwise those of the dense loop. The posteriors kernel writes only the
+// 16-component groups of a row that hold a non-zero posterior, with a 32-bit
+// group mask per row; the statistics kernel zero-fills the other groups
+// instead of reading them, so the posteriors' round trip through memory
+// carries the non-zero groups only. Every block writes its own statistics slot;
 // the finalise kernel reduces the slots in a fixed order, so no atomics touch
 // the result.
 //
@@ -86,32 +90,33 @@ __device__ __forceinline__ float ex2f_approx(float x) {
 
 constexpr int P_THREADS = 256;
 
-// Posteriors kernel: a warp owns 4 rows and every component (lane l holds
+// Posteriors kernel: a warp owns RR rows and every component (lane l holds
 // components c KCH + l CPL .. + CPL - 1 of each chunk c of KCH = 32 CPL), so a
 // row's log-likelihoods never leave registers and the row softmax is a pair
-// of warp shuffle reductions. The block (8 warps, 32 rows) stages only the
+// of warp shuffle reductions. The block (8 warps, 8 RR rows) stages only the
 // GMM slices and the descriptor slice, 8 dimensions at a time (double-buffered
-// by cp.async), so three blocks fit an SM at K <= 256 (a version that kept a
-// 64 x Kp log-likelihood block in shared memory fitted two and ran 10-17%
-// slower).
-constexpr int R_ROWS = 4;              // rows per warp
-constexpr int R_BM = 8 * R_ROWS;       // rows per block
+// by cp.async). Each GMM value read from shared memory serves RR rows: at
+// RR = 4 a warp's shared-memory wavefronts per dimension (17) match its FMA
+// cycles per SM (16), so K <= 256 takes RR = 8 (two blocks per SM, twice the
+// FMAs per load); larger K keeps RR = 4 (three blocks per SM at K <= 256
+// would need it, and 8 rows x 16 components of accumulators do not fit).
 constexpr int R_DS = 8;                // dimension slice
 
-template <int CPL, int NC>
-__global__ void __launch_bounds__(P_THREADS, (CPL * NC <= 8) ? 3 : 2)
+template <int CPL, int NC, int RR>
+__global__ void __launch_bounds__(P_THREADS, (CPL * NC <= 8 && RR == 4) ? 3 : 2)
 f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, const float *__restrict__ s_t,
                     const float *__restrict__ nms_t, const float *__restrict__ cst, float *__restrict__ gamma,
-                    float *__restrict__ lse) {
+                    uint32_t *__restrict__ gmask, float *__restrict__ lse) {
     constexpr int KCH = 32 * CPL;          // components per chunk
     constexpr int KT = KCH * NC;           // all (padded) components
-    constexpr int XS = R_BM + 4;
+    constexpr int BM = 8 * RR;             // rows per block
+    constexpr int XS = BM + 4;
     constexpr int STAGE = 2 * R_DS * KT + R_DS * XS;
     extern __shared__ __align__(16) float smem[];
 
     pdl_trigger();   // the statistics kernel may start launching (it waits for this grid)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * R_BM;
+    const int64_t row0 = (int64_t)blockIdx.x * BM;
     const int nslice = (D + R_DS - 1) / R_DS;
 
     auto issue = [&](int sl, int b) {
@@ -124,8 +129,9 @@ f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, co
             cp_async<16>(bS + dd * KT + c4, ok ? s_t + (size_t)d * Kp + c4 : s_t, ok);
             cp_async<16>(bN + dd * KT + c4, ok ? nms_t + (size_t)d * Kp + c4 : nms_t, ok);
         }
-        {   // the block's descriptor slice, dimension-major (R_BM * R_DS == P_THREADS)
-            const int r = tid / R_DS, dd = tid % R_DS, d = d0 + dd;
+#pragma unroll
+        for (int i = tid; i < BM * R_DS; i += P_THREADS) {   // the block's descriptor slice, dimension-major
+            const int r = i / R_DS, dd = i % R_DS, d = d0 + dd;
             const int64_t row = row0 + r;
             const bool ok = row < rows && d < D;
             cp_async<4>(bX + dd * XS + r, ok ? X + row * D + d : X, ok);
@@ -134,9 +140,9 @@ f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, co
     };
     issue(0, 0);
 
-    uint64_t acc[R_ROWS][NC][CPL / 2];
+    uint64_t acc[RR][NC][CPL / 2];
 #pragma unroll
-    for (int r = 0; r < R_ROWS; ++r)
+    for (int r = 0; r < RR; ++r)
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -151,8 +157,15 @@ f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, co
         const float *sS = smem + b * STAGE, *sN = sS + R_DS * KT, *sX = sN + R_DS * KT;
 #pragma unroll
         for (int dd = 0; dd < R_DS; ++dd) {
-            const float4 xv = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * R_ROWS]);
-            const uint64_t x2[R_ROWS] = {pk2(xv.x, xv.x), pk2(xv.y, xv.y), pk2(xv.z, xv.z), pk2(xv.w, xv.w)};
+            uint64_t x2[RR];
+#pragma unroll
+            for (int q = 0; q < RR / 4; ++q) {
+                const float4 xv = *reinterpret_cast<const float4 *>(&sX[dd * XS + warp * RR + 4 * q]);
+                x2[4 * q] = pk2(xv.x, xv.x);
+                x2[4 * q + 1] = pk2(xv.y, xv.y);
+                x2[4 * q + 2] = pk2(xv.z, xv.z);
+                x2[4 * q + 3] = pk2(xv.w, xv.w);
+            }
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 uint64_t s2[CPL / 2], n2[CPL / 2];
@@ -171,7 +184,7 @@ f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, co
                     n2[0] = pk2(o.x, o.y);
                 }
 #pragma unroll
-                for (int r = 0; r < R_ROWS; ++r)
+                for (int r = 0; r < RR; ++r)
 #pragma unroll
                     for (int p = 0; p < CPL / 2; ++p) {
                         const uint64_t t = fma2(x2[r], s2[p], n2[p]);
@@ -189,8 +202,8 @@ f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, co
 #pragma unroll
         for (int j = 0; j < CPL; ++j) cl[c][j] = cst[c * KCH + lane * CPL + j] * kLog2eF;
 #pragma unroll
-    for (int r = 0; r < R_ROWS; ++r) {
-        const int64_t row = row0 + warp * R_ROWS + r;
+    for (int r = 0; r < RR; ++r) {
+        const int64_t row = row0 + warp * RR + r;
         float y[NC][CPL];
         float m = -INFINITY;
 #pragma unroll
@@ -220,14 +233,30 @@ f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, co
         if (lse && lane == 0) lse[row] = (m + log2f(z)) * 0.69314718055994531f;
         const float iz = 1.0f / z;
         float *G = gamma + row * Kp;
+        // only the 16-component groups holding a non-zero posterior are
+        // written; the row's group mask tells the statistics kernel which
+        constexpr int L = 16 / CPL;   // lanes per group
+        uint32_t rmask = 0;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
+            float gv[CPL];
+            bool nz = false;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                gv[j] = y[c][j] * iz;
+                nz |= gv[j] != 0.f;
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, nz);
+#pragma unroll
+            for (int q = 0; q < 32 / L; ++q)
+                if ((bal >> (q * L)) & ((1u << L) - 1u)) rmask |= 1u << (c * (KCH / 16) + q);
+            if (!((bal >> ((lane / L) * L)) & ((1u << L) - 1u))) continue;
             if constexpr (CPL == 4)
-                *reinterpret_cast<float4 *>(G + c * KCH + lane * 4) =
-                    make_float4(y[c][0] * iz, y[c][1] * iz, y[c][2] * iz, y[c][3] * iz);
+                *reinterpret_cast<float4 *>(G + c * KCH + lane * 4) = make_float4(gv[0], gv[1], gv[2], gv[3]);
             else
-                *reinterpret_cast<float2 *>(G + c * KCH + lane * 2) = make_float2(y[c][0] * iz, y[c][1] * iz);
+                *reinterpret_cast<float2 *>(G + c * KCH + lane * 2) = make_float2(gv[0], gv[1]);
         }
+        if (lane == 0) gmask[row] = rmask;
     }
 }
 
@@ -249,7 +278,8 @@ constexpr int S_BLOCKS_PER_SM = 3;
 // block, the number of (row, 16-component group) pairs skipped and visited.
 template <bool VEC, bool THRESH>
 __global__ void __launch_bounds__(S_THREADS, S_BLOCKS_PER_SM)
-f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ gamma, int Kp, int Dp,
+f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ gamma,
+                 const uint32_t *__restrict__ gmask, int Kp, int Dp,
                  const float *__restrict__ mu_kd, const StatUnit *__restrict__ units, float *__restrict__ part,
                  int P, float tau, unsigned long long *__restrict__ skip_count) {
     __shared__ __align__(16) float sG[2][S_RS * S_KC];
@@ -269,16 +299,28 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     const int kb = kc0 + cg * S_CPT, dl = dg * S_DPT, db = dc0 + dl;
     const bool active = db < D;
 
-    // stage r0 -> buffer b: gamma[row][kc0..kc0+63] and X[row][dc0..dc0+63]
-    auto issue = [&](int r0, int b) {
+    // stage r0 -> buffer b: gamma[row][kc0..kc0+63] and X[row][dc0..dc0+63];
+    // a 16-component group whose mask bit is clear is zero-filled, not read.
+    // VEC: the 16-byte chunks of thread tid lie in rows tid/16 + 8q of the
+    // stage, whose masks (mk) are loaded one stage ahead.
+    constexpr int NQ = S_RS * S_KC / 4 / S_THREADS;
+    auto load_masks = [&](int r0, uint32_t (&mk)[NQ]) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int r = (tid >> 4) + q * (S_THREADS / 16);
+            mk[q] = r0 + r < u.nrows ? gmask[u.row0 + r0 + r] : 0u;
+        }
+    };
+    auto issue = [&](int r0, int b, const uint32_t (&mk)[NQ]) {
         if constexpr (VEC) {
 #pragma unroll
-            for (int q = 0; q < S_RS * S_KC / 4 / S_THREADS; ++q) {   // 16-byte chunks
+            for (int q = 0; q < NQ; ++q) {   // 16-byte chunks
                 const int i = tid + q * S_THREADS;
                 const int r = i >> 4, c4 = (i & 15) * 4;
                 const bool rok = r0 + r < u.nrows;
                 const int64_t row = u.row0 + r0 + r;
-                cp_async<16>(&sG[b][r * S_KC + c4], rok ? gamma + row * Kp + kc0 + c4 : gamma, rok);
+                const bool gok = rok && ((mk[q] >> ((kc0 + c4) >> 4)) & 1u);
+                cp_async<16>(&sG[b][r * S_KC + c4], gok ? gamma + row * Kp + kc0 + c4 : gamma, gok);
                 const bool xok = rok && dc0 + c4 < D;
                 cp_async<16>(&sXs[b][r * S_DC + c4], xok ? X + row * D + dc0 + c4 : X, xok);
             }
@@ -289,14 +331,18 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
                 const int r = i / S_KC, kk = i % S_KC;
                 const bool rok = r0 + r < u.nrows;
                 const int64_t row = u.row0 + r0 + r;
-                cp_async<4>(&sG[b][i], rok ? gamma + row * Kp + kc0 + kk : gamma, rok);
+                const bool gok = rok && ((gmask[row] >> ((kc0 + kk) >> 4)) & 1u);
+                cp_async<4>(&sG[b][i], gok ? gamma + row * Kp + kc0 + kk : gamma, gok);
                 const bool xok = rok && dc0 + kk < D;
                 cp_async<4>(&sXs[b][i], xok ? X + row * D + dc0 + kk : X, xok);
             }
         }
         cp_async_commit();
     };
-    issue(0, 0);
+    uint32_t mk[NQ];
+    if constexpr (VEC) load_masks(0, mk);
+    issue(0, 0, mk);
+    if constexpr (VEC) load_masks(S_RS, mk);
 
     uint64_t nm[S_CPT][S_DPT / 2], U[S_CPT][S_DPT / 2], W[S_CPT][S_DPT / 2];
     float S0[S_CPT];
@@ -316,8 +362,12 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     int buf = 0;
     unsigned skipped = 0, visited = 0;   // (row, 16-component group) pairs of this warp
     for (int r0 = 0; r0 < u.nrows; r0 += S_RS) {
-        if (r0 + S_RS < u.nrows) issue(r0 + S_RS, buf ^ 1);
-        else cp_async_commit();   // an empty group keeps the wait count uniform
+        if (r0 + S_RS < u.nrows) {
+            issue(r0 + S_RS, buf ^ 1, mk);
+            if constexpr (VEC) load_masks(r0 + 2 * S_RS, mk);
+        } else {
+            cp_async_commit();   // an empty group keeps the wait count uniform
+        }
         cp_async_wait1();         // this stage's copies (of this thread) have landed
         __syncthreads();          // ... and every thread's
         {
@@ -398,17 +448,17 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
 }  // namespace
 
 namespace {
-template <int CPL, int NC>
+template <int CPL, int NC, int RR = (CPL * NC <= 8 ? 8 : 4)>
 cudaError_t launch_post_reg(const fv_gmm *g, const float *X, int64_t rows, float *gamma, cudaStream_t st, float *lse) {
-    constexpr int KT = 32 * CPL * NC;
-    const size_t smem = sizeof(float) * 2 * (2 * R_DS * KT + R_DS * (R_BM + 4));
-    cudaError_t e = cudaFuncSetAttribute(f32_post_reg_kernel<CPL, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr int KT = 32 * CPL * NC, BM = 8 * RR;
+    const size_t smem = sizeof(float) * 2 * (2 * R_DS * KT + R_DS * (BM + 4));
+    cudaError_t e = cudaFuncSetAttribute(f32_post_reg_kernel<CPL, NC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     {
         KernelTimer kt_("f32_posteriors", st);
-        f32_post_reg_kernel<CPL, NC><<<(unsigned)((rows + R_BM - 1) / R_BM), P_THREADS, smem, st>>>(
-            X, rows, g->D, g->Kp, g->dev.s_t, g->dev.nms_t, g->dev.cst, gamma, lse);
+        f32_post_reg_kernel<CPL, NC, RR><<<(unsigned)((rows + BM - 1) / BM), P_THREADS, smem, st>>>(
+            X, rows, g->D, g->Kp, g->dev.s_t, g->dev.nms_t, g->dev.cst, gamma, f32_gamma_mask(gamma, rows, g->Kp), lse);
     }
     return cudaGetLastError();
 }
@@ -430,9 +480,9 @@ cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows,
     }
 }
 
-cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
-                             int n_units, float *part, int P, cudaStream_t st, bool pdl, float tau,
-                             unsigned long long *skip_count) {
+cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, int64_t rows,
+                             const StatUnit *units, int n_units, float *part, int P, cudaStream_t st, bool pdl,
+                             float tau, unsigned long long *skip_count) {
     if (n_units <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_units, (unsigned)(g->Kp / S_KC), (unsigned)((g->D + S_DC - 1) / S_DC));
     // 16-byte copies need 16-byte aligned rows of X (gamma rows always are)
@@ -442,7 +492,8 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
                     : (thr ? f32_stats_kernel<false, true> : f32_stats_kernel<false, false>);
     {
         KernelTimer kt_("f32_stats", st);
-        return launch_pdl(pdl, kern, grid, dim3(S_THREADS), 0, st, X, g->D, gamma, g->Kp, g->Dp, g->dev.mu_kd, units,
+        return launch_pdl(pdl, kern, grid, dim3(S_THREADS), 0, st, X, g->D, gamma,
+                          (const uint32_t *)f32_gamma_mask(const_cast<float *>(gamma), rows, g->Kp), g->Kp, g->Dp, g->dev.mu_kd, units,
                           part, P, tau, skip_count);
     }
     return cudaGetLastError();

@@ -144,14 +144,26 @@ cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// The FP32 posteriors buffer: rows x Kp floats, then one 32-bit mask per row
+// (bit j set when some posterior of components 16j .. 16j+15 is non-zero).
+// Only the 16-component groups with a set bit are written; the statistics
+// kernel reads only those and takes the others as the exact zeros they are.
+inline size_t f32_gamma_bytes(int64_t rows, int Kp) {
+    return sizeof(float) * (size_t)rows * Kp + sizeof(uint32_t) * (size_t)rows;
+}
+inline uint32_t *f32_gamma_mask(float *gamma, int64_t rows, int Kp) {
+    return reinterpret_cast<uint32_t *>(gamma + (size_t)rows * Kp);
+}
+
 // lse (nullable): per-row log sum_k exp(l_ik), natural log (EM log-likelihood).
 cudaError_t launch_f32_posteriors(const fv_gmm *g, const float *X, int64_t rows, float *gamma,
                                   cudaStream_t st, float *lse = nullptr);
+// gamma: the posteriors buffer of all `rows` rows the units index.
 // tau > 0: early termination (terms with posterior <= tau dropped, all-small
 // rows skipped); skip_count (device, nullable): [skipped, visited] counters.
-cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, const StatUnit *units,
-                             int n_units, float *part, int P, cudaStream_t st, bool pdl = false, float tau = 0.f,
-                             unsigned long long *skip_count = nullptr);
+cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma, int64_t rows,
+                             const StatUnit *units, int n_units, float *part, int P, cudaStream_t st,
+                             bool pdl = false, float tau = 0.f, unsigned long long *skip_count = nullptr);
 
 // Statistics slots are component-fastest: part[slot][j][Kp], j < P.
 // Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,

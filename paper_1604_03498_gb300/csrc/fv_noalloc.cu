@@ -67,7 +67,7 @@ __global__ void noalloc_plan_kernel(int64_t n, int64_t rpr, int nslots, FrameInf
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t scratch_bytes(int64_t N, int Kp, int K, int D, int P, int64_t nslots) {
-    return al256(sizeof(float) * (size_t)N * Kp) + al256(sizeof(float) * (size_t)nslots * Kp * P) +
+    return al256(f32_gamma_bytes(N, Kp)) + al256(sizeof(float) * (size_t)nslots * Kp * P) +
            al256(sizeof(FrameInfo)) + al256(sizeof(StatUnit) * (size_t)nslots) + al256(sizeof(double) * (size_t)(Kp / 32) * ((D + 7) / 8));
 }
 
@@ -119,7 +119,7 @@ extern "C" int fv_encode_noalloc(const fv_gmm *gmm, const float *X, int64_t N, f
     if (e != cudaSuccess) return cuda_fail(e, "fv_encode_noalloc: cudaGetSymbolAddress");
     char *b = (char *)base;
     float *gam = (float *)b;
-    b += al256(sizeof(float) * (size_t)rows * Kp);
+    b += al256(f32_gamma_bytes(rows, Kp));
     float *part = (float *)b;
     b += al256(sizeof(float) * (size_t)nslots * Kp * P);
     FrameInfo *frame = (FrameInfo *)b;
@@ -137,7 +137,7 @@ extern "C" int fv_encode_noalloc(const fv_gmm *gmm, const float *X, int64_t N, f
     if (N > 0) {
         if ((e = launch_f32_posteriors(gmm, X, N, gam, st)) != cudaSuccess)
             return cuda_fail(e, "fv_encode_noalloc: posteriors launch");
-        if ((e = launch_f32_stats(gmm, X, gam, units, nunits, part, P, st)) != cudaSuccess)
+        if ((e = launch_f32_stats(gmm, X, gam, N, units, nunits, part, P, st)) != cudaSuccess)
             return cuda_fail(e, "fv_encode_noalloc: statistics launch");
     }
     if ((e = launch_finalize(gmm, part, P, false, frame, 1, sq, fv_out, st, nullptr, nullptr, (int)nunits)) !=

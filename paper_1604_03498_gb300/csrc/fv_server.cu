@@ -10,8 +10,11 @@
 // order and alternates two batch plans on two streams: while one plan's graph
 // runs, the next batch is packed and launched on the other, so frames that
 // arrive while the GPU is busy are admitted into the next batch and their
-// work overlaps with the batch in flight. A host callback enqueued behind
+// work overlaps with the batch in flight. One kernel reads every frame of a
+// batch from its own device buffer and writes the plan's bfloat16 input rows
+// (no packed FP32 copy in between). A host callback enqueued behind
 // each batch's result copy stamps the completion time and wakes pollers.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -21,10 +24,31 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "fv_internal.h"
 
 namespace fv {
 namespace {
+
+// The batch's input in one pass: frame b's FP32 rows, still in the request's
+// own device buffer src[b], are rounded to bfloat16 and stored at rows
+// off[b] .. off[b+1]-1 of the plan's input (row pitch Dp, columns past D
+// zero). Grid (x, B): blockIdx.y is the frame, the x blocks stride over its
+// rows.
+__global__ void gather_convert_kernel(const float *const *__restrict__ src, const int64_t *__restrict__ off, int D,
+                                      int Dp, uint16_t *__restrict__ Xb) {
+    const int b = blockIdx.y;
+    const float *x = src[b];
+    const int64_t r0 = off[b], n = (off[b + 1] - r0) * Dp;
+    uint16_t *dst = Xb + r0 * Dp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / Dp;
+        const int d = (int)(i - r * Dp);
+        __nv_bfloat16 h = __float2bfloat16_rn(d < D ? x[r * D + d] : 0.f);
+        dst[i] = *reinterpret_cast<uint16_t *>(&h);
+    }
+}
 
 int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -56,7 +80,9 @@ struct fv_server {
     size_t fvlen = 0;
     fv_batch_plan *plan[2] = {nullptr, nullptr};
     cudaStream_t stream[2] = {nullptr, nullptr};
-    float *xpack[2] = {nullptr, nullptr};     // packed FP32 descriptors of a batch (device)
+    uint16_t *xin[2] = {nullptr, nullptr};    // the plans' bf16 input rows (device, owned by the plans)
+    void *table_h[2] = {nullptr, nullptr};    // a batch's source pointers and row offsets (pinned)
+    void *table_d[2] = {nullptr, nullptr};    // their device copy, read by the gather-convert kernel
     float *plan_out[2] = {nullptr, nullptr};  // plan output buffers (device)
     float *host_out[2] = {nullptr, nullptr};  // pinned copies of a batch's vectors
     std::vector<Request *> batch_reqs[2];
@@ -113,9 +139,30 @@ void CUDART_CB on_batch_done(void *arg) {
     s->cv_sched.notify_one();
 }
 
+size_t table_bytes(int max_frames) { return sizeof(float *) * max_frames + sizeof(int64_t) * (max_frames + 1); }
+
+// Uploads the batch's table (pinned; not rewritten before stream i's batch
+// completes) and converts every frame straight into the plan's input.
+int gather(fv_server *s, int i, int B, int64_t maxn) {
+    const cudaStream_t st = s->stream[i];
+    const int maxf = s->cfg.max_batch_frames;
+    cudaError_t e = cudaMemcpyAsync(s->table_d[i], s->table_h[i], table_bytes(maxf), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fv_server: table upload");
+    const int Dp = s->g->Dp;
+    const int64_t per_frame = (maxn * Dp + 255) / 256;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(per_frame, std::max(1, 8192 / B)));
+    const float *const *srcs = static_cast<const float *const *>(s->table_d[i]);
+    {
+        KernelTimer kt_("gather_convert", st);
+        gather_convert_kernel<<<dim3(gx, B), 256, 0, st>>>(srcs, reinterpret_cast<const int64_t *>(srcs + maxf),
+                                                           s->g->D, Dp, s->xin[i]);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "fv_server: gather-convert launch");
+}
+
 void scheduler(fv_server *s) {
     cudaSetDevice(s->device);
-    const int D = s->g->D;
     std::vector<int64_t> offs;
     while (true) {
         int i = -1;
@@ -152,23 +199,26 @@ void scheduler(fv_server *s) {
             s->batch_reqs[i] = take;
             ++s->n_batches;
         }
-        // pack, encode, copy back; every step ordered on stream i
-        offs.assign(take.size() + 1, 0);
+        // gather the frames into the plan's input, encode, copy back; every step ordered on stream i
+        const int B = (int)take.size();
+        offs.assign(B + 1, 0);
         const int64_t t = now_ns();
-        int rc = FV_OK;
-        for (size_t b = 0; b < take.size(); ++b) {
+        const float **srcs = static_cast<const float **>(s->table_h[i]);
+        int64_t maxn = 0;
+        for (int b = 0; b < B; ++b) {
             Request *r = take[b];
             r->t_launch = t;
             offs[b + 1] = offs[b] + r->n;
-            if (cudaMemcpyAsync(s->xpack[i] + offs[b] * D, r->dev, r->bytes, cudaMemcpyDeviceToDevice, s->stream[i]) !=
-                cudaSuccess)
-                rc = FV_ERR_CUDA;
+            srcs[b] = r->dev;
+            maxn = std::max(maxn, r->n);
+        }
+        std::memcpy(reinterpret_cast<int64_t *>(srcs + s->cfg.max_batch_frames), offs.data(), sizeof(int64_t) * (B + 1));
+        int rc = gather(s, i, B, maxn);
+        for (Request *r : take) {   // stream-ordered: freed once the gather has read them
             cudaFreeAsync(r->dev, s->stream[i]);
             r->dev = nullptr;
         }
-        if (rc == FV_OK)
-            rc = fv_batch_plan_run_f32(s->plan[i], s->xpack[i], offs.data(), (int)take.size(), nullptr, 1,
-                                       s->stream[i]);
+        if (rc == FV_OK) rc = fv_batch_plan_run(s->plan[i], offs.data(), B, nullptr, 1, s->stream[i]);
         if (rc == FV_OK &&
             cudaMemcpyAsync(s->host_out[i], s->plan_out[i], sizeof(float) * s->fvlen * take.size(),
                             cudaMemcpyDeviceToHost, s->stream[i]) != cudaSuccess)
@@ -212,7 +262,8 @@ void destroy_server(fv_server *s) {
     s->pending.clear();
     for (int i = 0; i < 2; ++i) {
         if (s->plan[i]) fv_batch_plan_destroy(s->plan[i]);
-        if (s->xpack[i]) cudaFree(s->xpack[i]);
+        if (s->table_h[i]) cudaFreeHost(s->table_h[i]);
+        if (s->table_d[i]) cudaFree(s->table_d[i]);
         if (s->host_out[i]) cudaFreeHost(s->host_out[i]);
         if (s->stream[i]) cudaStreamDestroy(s->stream[i]);
     }
@@ -229,6 +280,7 @@ extern "C" int fv_server_create(const fv_gmm *gmm, const fv_server_config *cfg, 
     if (!gmm || !cfg) return fail(FV_ERR_INVALID, "fv_server_create: NULL GMM or config");
     if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_server_create: needs an FV_PREC_BF16 GMM");
     if (cfg->max_slots < 1 || cfg->hbm_budget_bytes <= 0 || cfg->max_batch_frames < 1 ||
+        cfg->max_batch_frames > 65535 ||
         cfg->max_frame_descriptors < 1 || cfg->max_batch_descriptors < cfg->max_frame_descriptors)
         return fail(FV_ERR_INVALID, "fv_server_create: inconsistent configuration");
     fv_server *s = new fv_server();
@@ -246,11 +298,11 @@ extern "C" int fv_server_create(const fv_gmm *gmm, const fv_server_config *cfg, 
         for (int i = 0; i < 2 && rc == FV_OK; ++i) {
             fv_batch_plan_config pc{cfg->max_batch_frames, cfg->max_batch_descriptors, 0, nullptr};
             if ((rc = fv_batch_plan_create(gmm, &pc, &s->plan[i])) != FV_OK) break;
-            uint16_t *xin = nullptr;
-            fv_batch_plan_buffers(s->plan[i], &xin, &s->plan_out[i]);
+            fv_batch_plan_buffers(s->plan[i], &s->xin[i], &s->plan_out[i]);
             if ((e = cudaStreamCreateWithFlags(&s->stream[i], cudaStreamNonBlocking)) != cudaSuccess ||
-                (e = cudaMalloc(&s->xpack[i], sizeof(float) * (size_t)cfg->max_batch_descriptors * gmm->D)) !=
+                (e = cudaHostAlloc(&s->table_h[i], table_bytes(cfg->max_batch_frames), cudaHostAllocPortable)) !=
                     cudaSuccess ||
+                (e = cudaMalloc(&s->table_d[i], table_bytes(cfg->max_batch_frames))) != cudaSuccess ||
                 (e = cudaHostAlloc(&s->host_out[i], sizeof(float) * s->fvlen * cfg->max_batch_frames,
                                    cudaHostAllocPortable)) != cudaSuccess)
                 rc = cuda_fail(e, "fv_server_create: buffers");

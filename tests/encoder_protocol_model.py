@@ -151,6 +151,11 @@ def run(units_per_cluster, S, nstage, seed, drop=frozenset()):
             yield ('wait', B[f'LFULL{b}'], (i >> 1) & 1)
             check(st['L'][b] is not None and st['L'][b][0] == i and st['L'][b][1] != 'released', f'passA {i} {st["L"][b]}')
             yield ('step',)
+            # pass A keeps the exponentials in registers: the TMEM buffer is released at once
+            bl = B[f'LEMPTY{b}']
+            if bl.pending == 1:
+                st['L'][b][1] = 'released'
+            bl.arrive()
             if i > 0 and 'softmax_hxfree' not in drop:
                 yield ('wait', B[f'HXFREE{q}'], (i - 1) & 1)
             st['hx'][q][h] = i
@@ -183,14 +188,9 @@ def run(units_per_cluster, S, nstage, seed, drop=frozenset()):
                         check(st['xbuf'][j][pr][q] == i, f'xchg {i} changed')
             if i >= 1 and 'softmax_gfree' not in drop:
                 yield ('wait', B['GFREE'], (i - 1) & 1)
-            check(st['L'][b][0] == i, 'passB L')
             st['gam'][wid] = i
             yield ('step',)
             B['GFULL'].arrive()
-            bl = B[f'LEMPTY{b}']
-            if bl.pending == 1:
-                st['L'][b][1] = 'released'
-            bl.arrive()
             ui, first, last = tiles[i]
             if not last: continue
             yield ('wait', B['SDONE'], ui & 1)

@@ -119,6 +119,24 @@ def test_fp32_batch_equals_single_frames_bitwise():
         assert max_err(o, oracle_fv(f, w, mu, var)) <= TOL[P]
 
 
+def test_fp32_stale_posterior_scratch_is_never_read():
+    """The posteriors kernel writes only the 16-component groups that hold a
+    non-zero posterior (and a group mask per row); the statistics kernel
+    zero-fills the others. A frame encoded after a frame whose posteriors
+    were all non-zero (so the reused scratch holds non-zero values where the
+    second frame has exact zeros) gives bitwise the same vector as before."""
+    K, D, N = 64, 32, 3000
+    X, w, mu, var = case(K, D, N, 19)
+    a_st, a = gpu_encode(P, X, w, mu, var)
+    dense_var = var * 400.0   # every component overlaps every descriptor
+    Xd_, _, _, _ = case(K, D, N, 20)
+    gpu_encode(P, Xd_, w, mu, dense_var)
+    b_st, b = gpu_encode(P, X, w, mu, var)
+    assert a_st == b_st == fv.FV_OK
+    assert np.array_equal(a, b)
+    assert max_err(b, oracle_fv(X, w, mu, var)) <= TOL[P]
+
+
 def _golden():
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
     return sorted(os.path.join(here, f) for f in os.listdir(here) if f.endswith(".json"))
