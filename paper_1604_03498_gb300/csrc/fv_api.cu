@@ -255,9 +255,8 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
     }
     const int nslots = (int)plan.units.size();
     const int nctas = (int)plan.cta.size();
-    // floats per component in a statistics slot: BF16 [S1|S2hi|S2lo] blocks of
-    // D16 (the TMEM column layout) and S0; FP32 [A|B] blocks of D and S0
-    const int P = bf16 ? 3 * g->Dp + 1 : 2 * D + 1;
+    // floats per component in a statistics slot: centred [A|B] blocks of D and S0
+    const int P = 2 * D + 1;
     const int64_t ldx_dev = bf16 ? (x_bf16 ? ld_x : (int64_t)g->Dp) : (int64_t)D;
 
     Scratch s;
@@ -336,7 +335,7 @@ int encode_impl(const fv_gmm *g, const void *X, bool x_bf16, int64_t ld_x, const
         }
         int max_slots = 1;
         for (const FrameInfo &fi : plan.frames) max_slots = std::max(max_slots, fi.nslots);
-        if ((e = launch_finalize(g, part, P, bf16, frd, B, sq, outd, st, errd, nullptr, max_slots, true)) !=
+        if ((e = launch_finalize(g, part, P, frd, B, sq, outd, st, errd, nullptr, max_slots, true)) !=
             cudaSuccess) {
             rc = cuda_fail(e, "finalise launch");
             break;

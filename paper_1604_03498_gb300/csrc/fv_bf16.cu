@@ -22,9 +22,10 @@
 //      [S1 | S2hi | S2lo | S0] += gamma^T [X | X2hi | X2lo | 1]
 //    with the tile's own shared-memory X planes as the B operand; the
 //    accumulator stays in TMEM for a whole row share of one frame (a unit)
-//    and is then written to the unit's statistics slot (the paper's
-//    per-block copies of the statistics).
-// The finalise kernel centres the raw moments, scales and normalises.
+//    and is then centred (A = S1 - mu S0, B = S2 - 2 mu S1 + mu^2 S0) as
+//    it is written to the unit's statistics slot (the paper's per-block
+//    copies of the statistics).
+// The finalise kernels add the slots, scale and normalise.
 //
 // FV_PREC_BF16X2: the posteriors enter the statistics GEMM as a bf16 hi + lo
 // pair (gamma = hi + lo to about 2^-16, two MMAs per K step into the same
@@ -117,7 +118,9 @@ struct EncArgs {
     int S;          // CTAs per cluster (Kp / 128), each owning 128 components
     int nstage;     // Y-plane stages (1 or 2)
     int ny;         // 3*D16 + 16 columns of Y
-    int P;          // 3*D16 + 1 floats per component in a slot
+    int P;          // 2D + 1 floats per component in a slot: [A | B | S0], centred
+    int D;
+    const float *mu_t;        // [D][Kp] means (FP32), for the centring of the slot write-out
     const float *cl2;         // [Kp] log-constant times log2(e) (-inf on padding)
     const StatUnit *units;    // row ranges of one frame each
     const int2 *cl_units;     // per cluster: (first unit, number of units)
@@ -230,26 +233,73 @@ __device__ __forceinline__ void y_store(uint8_t *sy, uint4 (&x)[kHold], uint32_t
     }
 }
 
-// A softmax warp's share of a unit's statistics, TMEM -> slot (see the
-// flush in the kernel). Not inlined: it runs once per unit, and keeping it
-// out of the kernel body leaves the tile loop's code as it is.
-__device__ __noinline__ void write_stats(uint32_t ts, float *stg, float *dst0, int h, int P, int Kp, int lane) {
-    for (int n0 = h * 32; n0 < P; n0 += 64) {
-        uint32_t va[32];
-        tmem_ld32_issue(ts + n0, va);
-        tmem_ld_wait(va);
+// A softmax warp's share of a unit's statistics, TMEM -> slot, centred on the
+// way. For the lane's component (mean mu_d in dimension d) and each dimension
+// of the warp's 32-dimension chunks (h, h + 2, ...):
+//   A = S1 - mu S0,   B = S2 - 2 mu S1 + mu^2 S0 = fma(-mu, A, fma(-mu, S1, S2hi) + S2lo)
+// (the FMA order keeps each rounding relative to the centred quantities, and
+// centring is linear, so the shares' A and B add up to the frame's). A slot
+// then holds [A (D) | B (D) | S0] like the FP32 form's: 2D + 1 floats per
+// component instead of the raw moments' 3 D16 + 1. The first chunk's 32 means
+// are requested before the wait for the unit's last statistics MMA (SDONE,
+// parity `par`), so their latency hides behind it; each 16-dimension block of A and B goes through the
+// warp's own 4 KB of the gamma^T buffer (its pass-B rows, free until its next
+// pass B) as [16 A rows + 16 B rows][32 c], and each lane then stores 16 bytes
+// (4 components) of one row, so one warp store covers four 128-byte row
+// pieces. Not inlined: it runs once per unit, and keeping it out of the
+// kernel body leaves the tile loop's code as it is.
+// Returns false when the wait gave up (the kernel is aborting).
+__device__ __noinline__ bool write_stats(uint64_t *sdone, uint32_t par, volatile uint32_t *abort, uint32_t *err,
+                                         uint32_t ts, float *stg, float *dst0, const float *__restrict__ mu_t, int h,
+                                         int D, int D16, int Kp, int k, int lane) {
+    float mu[32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) stg[e * 32 + lane] = __uint_as_float(va[e]);
-        __syncwarp();
+    for (int e = 0; e < 32; ++e) mu[e] = h * 32 + e < D ? mu_t[(size_t)(h * 32 + e) * Kp + k] : 0.f;
+    if (!__all_sync(0xffffffffu, mbar_wait(sdone, par, abort, err))) return false;
+    tc_fence_after();
+    const float S0 = tmem_ld1(ts + 3 * D16);
+    if (h == 0) dst0[(size_t)(2 * D) * Kp + lane] = S0;
+    for (int d0 = h * 32; d0 < D; d0 += 64) {
+        if (d0 != h * 32) {
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            const int row = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
-            if (n0 + row < P)
-                *reinterpret_cast<float4 *>(dst0 + (size_t)(n0 + row) * Kp + c4) =
-                    *reinterpret_cast<const float4 *>(stg + row * 32 + c4);
+            for (int e = 0; e < 32; ++e) mu[e] = d0 + e < D ? mu_t[(size_t)(d0 + e) * Kp + k] : 0.f;
         }
-        __syncwarp();   // the block is read before the next group overwrites it
+#pragma unroll
+        for (int b16 = 0; b16 < 32; b16 += 16) {
+            if (d0 + b16 >= D) break;   // d0 + b16 + 16 <= D16
+            const uint32_t c = ts + (uint32_t)(d0 + b16);
+            uint32_t s1a[8], s2ha[8], s2la[8], s1b[8], s2hb[8], s2lb[8];
+            tmem_ld8_issue(c, s1a);
+            tmem_ld8_issue(c + D16, s2ha);
+            tmem_ld8_issue(c + 2 * D16, s2la);
+            tmem_ld8_issue(c + 8, s1b);
+            tmem_ld8_issue(c + D16 + 8, s2hb);
+            tmem_ld8_issue(c + 2 * D16 + 8, s2lb);
+            tmem_ld8_wait3(s1a, s2ha, s2la);
+            tmem_ld8_wait3(s1b, s2hb, s2lb);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float m = mu[b16 + e];
+                const float x1 = __uint_as_float(e < 8 ? s1a[e] : s1b[e - 8]);
+                const float x2h = __uint_as_float(e < 8 ? s2ha[e] : s2hb[e - 8]);
+                const float x2l = __uint_as_float(e < 8 ? s2la[e] : s2lb[e - 8]);
+                const float a = fmaf(-m, S0, x1);
+                stg[e * 32 + lane] = a;
+                stg[(16 + e) * 32 + lane] = fmaf(-m, a, fmaf(-m, x1, x2h) + x2l);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const int row = it * 4 + (lane >> 3), c4 = (lane & 7) * 4;
+                const int d = d0 + b16 + (row & 15);
+                if (d < D)
+                    *reinterpret_cast<float4 *>(dst0 + (size_t)(row < 16 ? d : D + d) * Kp + c4) =
+                        *reinterpret_cast<const float4 *>(stg + row * 32 + c4);
+            }
+            __syncwarp();   // the block is read before the next one overwrites it
+        }
     }
+    return true;
 }
 
 // Walks a cluster's units tile by tile (the current unit is held in registers).
@@ -492,8 +542,8 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         // row combine their (max, sum) through shared memory, then the
         // cluster's CTAs combine theirs; pass B rescales each chunk and writes
         // bf16 gamma^T to shared memory. After
-        // a unit's last tile the eight warps write the unit's statistics from
-        // TMEM to its slot (half the columns each).
+        // a unit's last tile the eight warps write the unit's centred
+        // statistics from TMEM to its slot (half the dimensions each).
         const int h = (warp - 4) >> 2, q = warp & 3;
         const int r = q * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
@@ -691,19 +741,14 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             w.next();
             ++i;
             if (!last) continue;
-            // the unit's statistics: TMEM -> slot part[slot][j][Kp]. Slot
-            // columns follow the TMEM columns ([S1 | S2hi | S2lo] blocks of
-            // D16, then S0, the first ones column), so this is a copy; warps
-            // 4-7 take 32-column groups 0, 2, ..., warps 8-11 groups 1, 3, ...
-            // Each group goes through the warp's own 4 KB of the gamma^T
-            // buffer (its pass-B rows, free until its next pass B): lane c
-            // writes its component's 32 values as column c of a [32 j][32 c]
-            // block, then each lane stores 16 bytes (4 components) of one j
-            // row, so one warp store covers four 128-byte row pieces.
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_SDONE], uidx & 1, abort_flag, p.err))) break;
-            tc_fence_after();
-            write_stats(lane_base + kStatCol, reinterpret_cast<float *>(smem + L.g + h * kGHalf + q * 32 * 128),
-                        p.part + (size_t)uslot * p.Kp * p.P + (size_t)rank * kComps + q * 32, h, p.P, p.Kp, lane);
+            // the unit's statistics: TMEM -> slot part[slot][j][Kp], centred
+            // (write_stats); the warps of one lane quadrant split the
+            // dimensions in 32-wide chunks
+            if (!write_stats(&bars[EB_SDONE], uidx & 1, abort_flag, p.err, lane_base + kStatCol,
+                             reinterpret_cast<float *>(smem + L.g + h * kGHalf + q * 32 * 128),
+                             p.part + (size_t)uslot * p.Kp * p.P + (size_t)rank * kComps + q * 32, p.mu_t, h, p.D,
+                             p.nkb * 16, p.Kp, (int)rank * kComps + q * 32 + lane, lane))
+                break;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars[EB_TEMPTY]);
@@ -855,7 +900,7 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
         c.nstage = nstage;
         c.smem = enc_smem(c.nkb, c.S, c.nstage, c.glo).total;
     }
-    if (P != 3 * c.nkb * 16 + 1) return fail(FV_ERR_INVALID, "BF16 form: slot width mismatch");
+    if (P != 2 * g->D + 1) return fail(FV_ERR_INVALID, "BF16 form: slot width mismatch");
     if (rows > (int64_t)INT32_MAX - 256) return fail(FV_ERR_UNSUPPORTED, "BF16 form: too many rows for one call");
 
     CUtensorMap tmX, tmB;
@@ -870,6 +915,8 @@ int run_bf16_encoder(const fv_gmm *g, const uint16_t *Xb, int64_t ldx, int64_t r
     a.nstage = c.nstage;
     a.ny = c.ny;
     a.P = P;
+    a.D = g->D;
+    a.mu_t = g->dev.mu_t;
     a.cl2 = g->dev.cl2;
     a.units = units;
     a.cl_units = cl_units;

@@ -18,7 +18,7 @@ cudaError_t launch_bf16_convert(const fv_gmm *g, const float *X, int64_t rows, u
 // Xb: bf16 rows of pitch ldx; rows: rows addressable in Xb (rows past it read as zero).
 // units: row ranges (one frame each) grouped per share; cl_units[c] = (first
 // unit, count) of share c, which one cluster of the kernel walks.
-// part: [slot][P][Kp] statistics slots, P = 3*D16 + 1.
+// part: [slot][P][Kp] statistics slots, P = 2D + 1 (centred [A | B | S0]).
 // err: device word a kernel sets when a bounded wait gives up (zeroed by the caller).
 // tau > 0: early termination (posteriors <= tau dropped, all-zero 16-row
 // K steps of the statistics GEMM skipped); skip_count (device, nullable):

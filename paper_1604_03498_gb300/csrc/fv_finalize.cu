@@ -19,13 +19,9 @@
 // values by 1/||z||.
 //
 // All per-element arithmetic is FP32 (GB300's FP64 rate is a small fraction
-// of its FP32 rate). The BF16 form's raw moments are centred with FMAs whose
-// rounding is relative to the centred quantities:
-//   a  = S1 - mu S0                  = fma(-mu, S0, S1)
-//   b  = S2 - mu S1                  = fma(-mu, S1, S2hi) + S2lo
-//   M2 = S2 - 2 mu S1 + mu^2 S0      = b - mu a = fma(-mu, a, b)
-//   u  = a / sigma * alpha / N,   v = (M2 / sigma^2 - S0) * beta / N.
-// FP32 form slots hold centred sums A = sum g (x-mu), B = sum g (x-mu)^2:
+// of its FP32 rate). Slots of both forms hold centred sums (the BF16 encoder
+// centres its raw moments as it writes them out):
+//   A = sum g (x - mu),  B = sum g (x - mu)^2,  S0 = sum g
 //   u = A / sigma * alpha / N,    v = (B / sigma^2 - S0) * beta / N.
 #include "fv_internal.h"
 
@@ -95,7 +91,6 @@ finalize_r_kernel(float *__restrict__ part, int P, int Kp, bool split, const Fra
 }
 
 // grid (Kp/32, ceil(D/8), frames); thread (lane -> component, grp -> dimension)
-template <bool RAW>
 __global__ void __launch_bounds__(FA_THREADS)
 finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, const FrameInfo *__restrict__ frames,
                   GmmDev g, double *__restrict__ sq, float *__restrict__ out, const int *__restrict__ B_dev) {
@@ -117,25 +112,13 @@ finalize_a_kernel(const float *__restrict__ part, int P, int Kp, int K, int D, c
     if (d < D && k < K && fr.n > 0) {
         const float *ps = part + (size_t)fr.slot0 * sstride + k;   // the frame totals
         const float S0 = ps[(size_t)(P - 1) * Kp];
-        const int jb = RAW ? (P - 1) / 3 : D;   // statistic block width (D16 for BF16 slots)
-        const float s1 = ps[(size_t)d * Kp];
-        const float s2 = ps[(size_t)(jb + d) * Kp];
+        const float a = ps[(size_t)d * Kp];
+        const float b = ps[(size_t)(D + d) * Kp];
         const float inv_n = 1.0f / (float)fr.n;
         const float al = g.alpha[k] * inv_n, be = g.beta[k] * inv_n;
         const float isd = g.s_t[(size_t)d * Kp + k], pr = g.prec_t[(size_t)d * Kp + k];
-        float u, v;
-        if (RAW) {
-            const float s3 = ps[(size_t)(2 * jb + d) * Kp];
-            const float m = g.mu_t[(size_t)d * Kp + k];
-            const float a = fmaf(-m, S0, s1);
-            const float b = fmaf(-m, s1, s2) + s3;
-            const float m2 = fmaf(-m, a, b);
-            u = a * isd * al;
-            v = fmaf(m2, pr, -S0) * be;
-        } else {
-            u = s1 * isd * al;
-            v = fmaf(s2, pr, -S0) * be;
-        }
+        const float u = a * isd * al;
+        const float v = fmaf(b, pr, -S0) * be;
         zu = ssqrtf(u);
         zv = ssqrtf(v);
     }
@@ -215,7 +198,7 @@ cudaError_t launch_slot_reduce(const fv_gmm *g, float *part, int P, const FrameI
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments, const FrameInfo *frames,
+cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, const FrameInfo *frames,
                             int B, double *sq, float *out, cudaStream_t st, const uint32_t *err, const int *B_dev,
                             int max_slots, bool pdl) {
     if (B <= 0) return cudaSuccess;
@@ -233,7 +216,7 @@ cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moment
     dim3 grid_a((unsigned)nbx, (unsigned)nby, (unsigned)B);
     {
         KernelTimer kt_("finalize_a", st);
-        e = launch_pdl(pdl, raw_moments ? finalize_a_kernel<true> : finalize_a_kernel<false>, grid_a, dim3(FA_THREADS),
+        e = launch_pdl(pdl, finalize_a_kernel, grid_a, dim3(FA_THREADS),
                        0, st, (const float *)part, P, g->Kp, g->K, g->D, frames, g->dev, sq, out, B_dev);
     }
     if (e != cudaSuccess) return e;

@@ -167,9 +167,8 @@ cudaError_t launch_f32_stats(const fv_gmm *g, const float *X, const float *gamma
 
 // Statistics slots are component-fastest: part[slot][j][Kp], j < P.
 // Finalise: reduce per-range statistics in a fixed order, scale, signed sqrt,
-// L2. raw_moments selects the BF16 form's [S1, S2hi, S2lo, S0] layout
-// (blocks of D16 = D rounded up to 16, P = 3*D16+1) over the FP32 form's
-// centred [A, B, S0] layout (blocks of D, P = 2D+1).
+// L2. Slots of both forms hold the centred [A, B, S0] layout (blocks of D,
+// P = 2D+1).
 // sq needs B * (Kp / 32) * ceil(D / 8) doubles. Each frame's first slot is
 // overwritten with the frame's totals (three launches: slot reduction,
 // encode, normalise). max_slots: the most slots a frame has (any value is
@@ -185,7 +184,7 @@ cudaError_t launch_slot_reduce(const fv_gmm *g, float *part, int P, const FrameI
 // true, ld a multiple of 16); err: device word set if an MMA wait expired.
 cudaError_t launch_pca(const fv_pca *p, const float *X, const float *xy, int64_t N, bool bf16, void *Y, int ld,
                        uint32_t *err, cudaStream_t st);
-cudaError_t launch_finalize(const fv_gmm *g, float *part, int P, bool raw_moments,
+cudaError_t launch_finalize(const fv_gmm *g, float *part, int P,
                             const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
                             const uint32_t *err = nullptr, const int *B_dev = nullptr, int max_slots = 1,
                             bool pdl = false);

@@ -140,7 +140,7 @@ extern "C" int fv_encode_noalloc(const fv_gmm *gmm, const float *X, int64_t N, f
         if ((e = launch_f32_stats(gmm, X, gam, N, units, nunits, part, P, st)) != cudaSuccess)
             return cuda_fail(e, "fv_encode_noalloc: statistics launch");
     }
-    if ((e = launch_finalize(gmm, part, P, false, frame, 1, sq, fv_out, st, nullptr, nullptr, (int)nunits)) !=
+    if ((e = launch_finalize(gmm, part, P, frame, 1, sq, fv_out, st, nullptr, nullptr, (int)nunits)) !=
         cudaSuccess)
         return cuda_fail(e, "fv_encode_noalloc: finalise launch");
     if (N == 0) return fail(FV_ERR_EMPTY, "no descriptors (N == 0)");

@@ -142,7 +142,7 @@ int launch_sequence(fv_batch_plan *p, int G, cudaStream_t st) {
                               (const int2 *)(p->wl + p->off_cta), G, p->part, p->P, p->err, st, 0.f, nullptr,
                               p->nstage);
     if (rc != FV_OK) return rc;
-    if ((e = launch_finalize(g, p->part, p->P, true, (const FrameInfo *)(p->wl + p->off_frames), p->max_frames, p->sq,
+    if ((e = launch_finalize(g, p->part, p->P, (const FrameInfo *)(p->wl + p->off_frames), p->max_frames, p->sq,
                              p->out, st, p->err, B_dev)) != cudaSuccess)
         return cuda_fail(e, "batch plan: finalise launch");
     return FV_OK;
@@ -238,7 +238,7 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
     p->base = bf16_max_shares(gmm, p->sms);
     p->max_frames = cfg->max_frames;
     p->max_rows = cfg->max_rows;
-    p->P = 3 * gmm->Dp + 1;
+    p->P = 2 * gmm->D + 1;
     p->Gmax = 4 * p->base;
     p->nstage = bf16_max_stages(gmm);
     p->G = p->base;

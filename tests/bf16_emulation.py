@@ -12,7 +12,9 @@ a GPU:
   c = log w - 1/2 sum log sigma^2 - 1/2 sum mu^2/sigma^2 (Sec. 3.1 expanded);
 * the posteriors are rounded to bfloat16 before the statistics GEMM
   gamma^T [X | X^2hi | X^2lo | 1];
-* the finalise centres the raw moments and applies the Sec. 4 encoding.
+* the raw moments are centred (the encoder does it as it writes each share's
+  slot; centring is linear, so one frame-wide centring stands for it here)
+  and the Sec. 4 encoding is applied.
 
 Any term can be switched off (``drop``) or the posterior rounding changed
 (``gamma``: "bf16", "fp16", "hilo" for a bf16 hi + lo pair, "exact"), which
