@@ -26,7 +26,8 @@
 // 16-component groups of a row that hold a non-zero posterior, with a 32-bit
 // group mask per row; the statistics kernel zero-fills the other groups
 // instead of reading them, so the posteriors' round trip through memory
-// carries the non-zero groups only. Every block writes its own statistics slot;
+// carries the non-zero groups only, and each statistics block first lists
+// the rows with a non-zero group in its 64 components and stages only those. Every block writes its own statistics slot;
 // the finalise kernel reduces the slots in a fixed order, so no atomics touch
 // the result.
 //
@@ -268,6 +269,7 @@ constexpr int S_DPT = 8;   // dimensions per thread
 constexpr int S_THREADS = (S_KC / S_CPT) * (S_DC / S_DPT);  // 128
 
 constexpr int S_BLOCKS_PER_SM = 3;
+constexpr int S_WIN = 512;  // rows per compaction window (row offsets fit 16 bits)
 
 // grid.x = statistics units (row ranges), grid.y = 64-component chunks,
 // grid.z = 64-dimension chunks. Stages of 32 rows are double-buffered in
@@ -284,6 +286,8 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
                  int P, float tau, unsigned long long *__restrict__ skip_count) {
     __shared__ __align__(16) float sG[2][S_RS * S_KC];
     __shared__ __align__(16) float sXs[2][S_RS * S_DC];
+    __shared__ uint32_t sList[S_WIN];
+    __shared__ int sWarpCnt[S_THREADS / 32];
 
     pdl_wait();      // the posteriors are complete
     pdl_trigger();
@@ -298,51 +302,6 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
     const int cg = (tid >> 5) * 4 + (tid & 3), dg = (tid & 31) >> 2;
     const int kb = kc0 + cg * S_CPT, dl = dg * S_DPT, db = dc0 + dl;
     const bool active = db < D;
-
-    // stage r0 -> buffer b: gamma[row][kc0..kc0+63] and X[row][dc0..dc0+63];
-    // a 16-component group whose mask bit is clear is zero-filled, not read.
-    // VEC: the 16-byte chunks of thread tid lie in rows tid/16 + 8q of the
-    // stage, whose masks (mk) are loaded one stage ahead.
-    constexpr int NQ = S_RS * S_KC / 4 / S_THREADS;
-    auto load_masks = [&](int r0, uint32_t (&mk)[NQ]) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int r = (tid >> 4) + q * (S_THREADS / 16);
-            mk[q] = r0 + r < u.nrows ? gmask[u.row0 + r0 + r] : 0u;
-        }
-    };
-    auto issue = [&](int r0, int b, const uint32_t (&mk)[NQ]) {
-        if constexpr (VEC) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {   // 16-byte chunks
-                const int i = tid + q * S_THREADS;
-                const int r = i >> 4, c4 = (i & 15) * 4;
-                const bool rok = r0 + r < u.nrows;
-                const int64_t row = u.row0 + r0 + r;
-                const bool gok = rok && ((mk[q] >> ((kc0 + c4) >> 4)) & 1u);
-                cp_async<16>(&sG[b][r * S_KC + c4], gok ? gamma + row * Kp + kc0 + c4 : gamma, gok);
-                const bool xok = rok && dc0 + c4 < D;
-                cp_async<16>(&sXs[b][r * S_DC + c4], xok ? X + row * D + dc0 + c4 : X, xok);
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < S_RS * S_KC / S_THREADS; ++q) {
-                const int i = tid + q * S_THREADS;
-                const int r = i / S_KC, kk = i % S_KC;
-                const bool rok = r0 + r < u.nrows;
-                const int64_t row = u.row0 + r0 + r;
-                const bool gok = rok && ((gmask[row] >> ((kc0 + kk) >> 4)) & 1u);
-                cp_async<4>(&sG[b][i], gok ? gamma + row * Kp + kc0 + kk : gamma, gok);
-                const bool xok = rok && dc0 + kk < D;
-                cp_async<4>(&sXs[b][i], xok ? X + row * D + dc0 + kk : X, xok);
-            }
-        }
-        cp_async_commit();
-    };
-    uint32_t mk[NQ];
-    if constexpr (VEC) load_masks(0, mk);
-    issue(0, 0, mk);
-    if constexpr (VEC) load_masks(S_RS, mk);
 
     uint64_t nm[S_CPT][S_DPT / 2], U[S_CPT][S_DPT / 2], W[S_CPT][S_DPT / 2];
     float S0[S_CPT];
@@ -359,61 +318,123 @@ f32_stats_kernel(const float *__restrict__ X, int D, const float *__restrict__ g
         }
     }
 
+    // The unit's rows in windows of S_WIN. First the window's live rows (some
+    // posterior of the block's 64 components non-zero, from the group masks)
+    // are listed in increasing order as (row - w0) | (group bits << 16); a row
+    // whose four groups are all zero would add exact zeros, so it is neither
+    // staged nor visited (the early-termination counts take it as visited and
+    // skipped by every warp). Then the listed rows are staged 32 at a time,
+    // double-buffered: entries l0..l0+31 -> buffer b, gamma[row][kc0..kc0+63]
+    // (a group whose bit is clear zero-filled, not read) and X[row][dc0..dc0+63].
+    auto issue = [&](int w0, int l0, int nlive, int b) {
+        if constexpr (VEC) {
+#pragma unroll
+            for (int q = 0; q < S_RS * S_KC / 4 / S_THREADS; ++q) {   // 16-byte chunks
+                const int i = tid + q * S_THREADS;
+                const int r = i >> 4, c4 = (i & 15) * 4;
+                const bool rok = l0 + r < nlive;
+                const uint32_t e = rok ? sList[l0 + r] : 0u;
+                const int64_t row = u.row0 + w0 + (int)(e & 0xFFFFu);
+                const bool gok = rok && ((e >> (16 + (c4 >> 4))) & 1u);
+                cp_async<16>(&sG[b][r * S_KC + c4], gok ? gamma + row * Kp + kc0 + c4 : gamma, gok);
+                const bool xok = rok && dc0 + c4 < D;
+                cp_async<16>(&sXs[b][r * S_DC + c4], xok ? X + row * D + dc0 + c4 : X, xok);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < S_RS * S_KC / S_THREADS; ++q) {
+                const int i = tid + q * S_THREADS;
+                const int r = i / S_KC, kk = i % S_KC;
+                const bool rok = l0 + r < nlive;
+                const uint32_t e = rok ? sList[l0 + r] : 0u;
+                const int64_t row = u.row0 + w0 + (int)(e & 0xFFFFu);
+                const bool gok = rok && ((e >> (16 + (kk >> 4))) & 1u);
+                cp_async<4>(&sG[b][i], gok ? gamma + row * Kp + kc0 + kk : gamma, gok);
+                const bool xok = rok && dc0 + kk < D;
+                cp_async<4>(&sXs[b][i], xok ? X + row * D + dc0 + kk : X, xok);
+            }
+        }
+        cp_async_commit();
+    };
+
     int buf = 0;
     unsigned skipped = 0, visited = 0;   // (row, 16-component group) pairs of this warp
-    for (int r0 = 0; r0 < u.nrows; r0 += S_RS) {
-        if (r0 + S_RS < u.nrows) {
-            issue(r0 + S_RS, buf ^ 1, mk);
-            if constexpr (VEC) load_masks(r0 + 2 * S_RS, mk);
-        } else {
-            cp_async_commit();   // an empty group keeps the wait count uniform
+    for (int w0 = 0; w0 < u.nrows; w0 += S_WIN) {
+        const int wn = min(S_WIN, u.nrows - w0);
+        int nlive = 0;
+#pragma unroll
+        for (int q = 0; q < S_WIN / S_THREADS; ++q) {   // the window's live rows, in order
+            const int r = q * S_THREADS + tid;
+            const uint32_t gb = r < wn ? (gmask[u.row0 + w0 + r] >> (kc0 >> 4)) & 0xFu : 0u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, gb != 0u);
+            if ((tid & 31) == 0) sWarpCnt[tid >> 5] = __popc(bal);
+            __syncthreads();
+            int base = nlive, tot = 0;
+#pragma unroll
+            for (int w = 0; w < S_THREADS / 32; ++w) {
+                base += w < (tid >> 5) ? sWarpCnt[w] : 0;
+                tot += sWarpCnt[w];
+            }
+            if (gb) sList[base + __popc(bal & ((1u << (tid & 31)) - 1u))] = (uint32_t)r | (gb << 16);
+            nlive += tot;
+            __syncthreads();   // the counts are read before the next pass writes them; the list is complete
         }
-        cp_async_wait1();         // this stage's copies (of this thread) have landed
-        __syncthreads();          // ... and every thread's
-        {
-            const float *G = sG[buf];
-            const float *Xs = sXs[buf];
-            // the operands of row r + 1 are loaded while row r is accumulated
-            float4 g4 = *reinterpret_cast<const float4 *>(&G[cg * S_CPT]);
-            float4 xa = *reinterpret_cast<const float4 *>(&Xs[dl]);
-            float4 xb = *reinterpret_cast<const float4 *>(&Xs[dl + 4]);
+        if constexpr (THRESH) {
+            visited += (unsigned)(wn - nlive);
+            skipped += (unsigned)(wn - nlive);
+        }
+        if (nlive == 0) continue;
+        issue(w0, 0, nlive, buf);
+        for (int l0 = 0; l0 < nlive; l0 += S_RS) {
+            if (l0 + S_RS < nlive) issue(w0, l0 + S_RS, nlive, buf ^ 1);
+            else cp_async_commit();   // an empty group keeps the wait count uniform
+            cp_async_wait1();         // this stage's copies (of this thread) have landed
+            __syncthreads();          // ... and every thread's
+            {
+                const float *G = sG[buf];
+                const float *Xs = sXs[buf];
+                // the operands of row r + 1 are loaded while row r is accumulated
+                float4 g4 = *reinterpret_cast<const float4 *>(&G[cg * S_CPT]);
+                float4 xa = *reinterpret_cast<const float4 *>(&Xs[dl]);
+                float4 xb = *reinterpret_cast<const float4 *>(&Xs[dl + 4]);
 #pragma unroll 4
-            for (int r = 0; r < S_RS; ++r) {
-                float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-                const uint64_t xv[4] = {pk2(xa.x, xa.y), pk2(xa.z, xa.w), pk2(xb.x, xb.y), pk2(xb.z, xb.w)};
-                if (r + 1 < S_RS) {
-                    g4 = *reinterpret_cast<const float4 *>(&G[(r + 1) * S_KC + cg * S_CPT]);
-                    xa = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl]);
-                    xb = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl + 4]);
-                }
-                if constexpr (THRESH) {
-#pragma unroll
-                    for (int c = 0; c < S_CPT; ++c) gv[c] = gv[c] > tau ? gv[c] : 0.f;   // dropped terms
-                    if (r0 + r < u.nrows) ++visited;
-                }
-                const bool nz = (gv[0] != 0.f) | (gv[1] != 0.f) | (gv[2] != 0.f) | (gv[3] != 0.f);
-                if (!__any_sync(0xffffffffu, nz)) {   // exact zeros (or dropped terms) for all 16 components
-                    if constexpr (THRESH) {
-                        if (r0 + r < u.nrows) ++skipped;
+                for (int r = 0; r < S_RS; ++r) {
+                    float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+                    const uint64_t xv[4] = {pk2(xa.x, xa.y), pk2(xa.z, xa.w), pk2(xb.x, xb.y), pk2(xb.z, xb.w)};
+                    if (r + 1 < S_RS) {
+                        g4 = *reinterpret_cast<const float4 *>(&G[(r + 1) * S_KC + cg * S_CPT]);
+                        xa = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl]);
+                        xb = *reinterpret_cast<const float4 *>(&Xs[(r + 1) * S_DC + dl + 4]);
                     }
-                    continue;
-                }
+                    if constexpr (THRESH) {
 #pragma unroll
-                for (int c = 0; c < S_CPT; ++c) {
-                    S0[c] += gv[c];
-                    const uint64_t g2 = pk2(gv[c], gv[c]);
+                        for (int c = 0; c < S_CPT; ++c) gv[c] = gv[c] > tau ? gv[c] : 0.f;   // dropped terms
+                        if (l0 + r < nlive) ++visited;
+                    }
+                    const bool nz = (gv[0] != 0.f) | (gv[1] != 0.f) | (gv[2] != 0.f) | (gv[3] != 0.f);
+                    if (!__any_sync(0xffffffffu, nz)) {   // exact zeros (or dropped terms) for all 16 components
+                        if constexpr (THRESH) {
+                            if (l0 + r < nlive) ++skipped;
+                        }
+                        continue;
+                    }
 #pragma unroll
-                    for (int j = 0; j < S_DPT / 2; ++j) {
-                        const uint64_t dx = add2(xv[j], nm[c][j]);
-                        const uint64_t gd = mul2(g2, dx);
-                        U[c][j] = add2(U[c][j], gd);
-                        W[c][j] = fma2(gd, dx, W[c][j]);
+                    for (int c = 0; c < S_CPT; ++c) {
+                        S0[c] += gv[c];
+                        const uint64_t g2 = pk2(gv[c], gv[c]);
+#pragma unroll
+                        for (int j = 0; j < S_DPT / 2; ++j) {
+                            const uint64_t dx = add2(xv[j], nm[c][j]);
+                            const uint64_t gd = mul2(g2, dx);
+                            U[c][j] = add2(U[c][j], gd);
+                            W[c][j] = fma2(gd, dx, W[c][j]);
+                        }
                     }
                 }
             }
+            __syncthreads();   // the buffer is consumed before it is refilled
+            buf ^= 1;
         }
-        __syncthreads();   // the buffer is consumed before it is refilled
-        buf ^= 1;
     }
     if constexpr (THRESH) {
         if (skip_count && (threadIdx.x & 31) == 0 && dc0 == 0) {   // one count per warp and component group
