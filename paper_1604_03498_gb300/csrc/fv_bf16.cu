@@ -32,8 +32,11 @@
 // accumulator), so the statistics carry the posteriors' FP32 values instead
 // of their bfloat16 rounding (2^-9 relative). That rounding is the largest
 // error of the precision form, and the improved-FV scaling 1/(N sqrt(w))
-// magnifies it for components of very small prior w. The doubled gamma^T tile
-// leaves room for one Y stage at D = 64 (two at D <= 48).
+// magnifies it for components of very small prior w. The hi + lo pair of a
+// tile goes through the plain form's 32 KB gamma^T buffer in two 64-row
+// halves: lane quadrants 0-1 write rows 0-63, the statistics GEMM reads them,
+// then quadrants 2-3 write rows 64-127 (each half with its own full / free
+// barriers), so the form keeps the plain form's Y stages (two at D = 64).
 //
 // Early termination (Sec. 3.3, Algorithm 5), as block sparsity of the
 // statistics GEMM: with a posterior threshold tau > 0 the softmax writes
@@ -81,6 +84,7 @@ constexpr int kRows = 128;             // row tile: M of the first GEMM, K of th
 constexpr int kComps = 128;            // components per CTA: N of the first GEMM, M of the second
 constexpr uint32_t kBlk = kRows * 32u;           // one [128][16] bf16 block with 32-byte rows (4 KB)
 constexpr uint32_t kGHalf = 64u * kRows * 2u;    // 64 components x 128 rows of gamma^T (16 KB)
+constexpr uint32_t kSub = kGHalf / 2u;           // 64 components x 64 rows (BF16X2 halves, 8 KB)
 constexpr uint32_t kStatCol = 2u * kComps;       // first TMEM column of the statistics accumulator
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxSmem = 232448;
@@ -146,8 +150,8 @@ __host__ __device__ inline EncSmem enc_smem(int nkb, int S, int nstage, bool glo
     s.y_stage = (3u * nkb + 1u) * kBlk;          // [X | X2hi | X2lo | 1] blocks of 128 rows
     s.y = off;
     off += nstage * s.y_stage;
-    s.g = off;                                   // gamma^T: two 64-component halves (then the lo pair's)
-    off += (glo ? 4u : 2u) * kGHalf;
+    s.g = off;                                   // gamma^T: two 64-component halves (BF16X2: hi | lo of 64 rows)
+    off += 2u * kGHalf;
     s.hx = off;                                  // (max, sum) per row of each column half
     off += 2u * kRows * 8u;
     s.xchg = off;                                // (max, sum) per row: 2 slots x S ranks
@@ -185,7 +189,9 @@ enum {
     EB_HXFULL = 19,   // [4] both column halves of a quadrant's rows have written (max, sum)
     EB_HXFREE = 23,   // [4] both halves have read them
     EB_XRFREE = 27,   // the builders hold a tile's x in registers: the landing buffer may refill
-    EB_NBARS = 28
+    EB_GFULL2 = 28,   // BF16X2: gamma^T hi + lo of rows 64-127 written (EB_GFULL: rows 0-63)
+    EB_GFREE2 = 29,   // BF16X2: statistics GEMM done with rows 64-127 (EB_GFREE: rows 0-63)
+    EB_NBARS = 30
 };
 
 // Y planes of one tile, built in two steps so that only the stores wait for
@@ -243,8 +249,10 @@ __device__ __forceinline__ void y_store(uint8_t *sy, uint4 (&x)[kHold], uint32_t
 // component instead of the raw moments' 3 D16 + 1. The first chunk's 32 means
 // are requested before the wait for the unit's last statistics MMA (SDONE,
 // parity `par`), so their latency hides behind it; each 16-dimension block of A and B goes through the
-// warp's own 4 KB of the gamma^T buffer (its pass-B rows, free until its next
-// pass B) as [16 A rows + 16 B rows][32 c], and each lane then stores 16 bytes
+// warp's own 4 KB of the gamma^T buffer (its pass-B rows in the plain form;
+// the buffer is free of posteriors once the unit's last statistics MMA is
+// done, and BF16X2's next pass B waits for this write-out) as
+// [16 A rows + 16 B rows][32 c], and each lane then stores 16 bytes
 // (4 components) of one row, so one warp store covers four 128-byte row
 // pieces. Not inlined: it runs once per unit, and keeping it out of the
 // kernel body leaves the tile loop's code as it is.
@@ -365,7 +373,11 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             mbar_init(&bars[EB_LEMPTY + s], 8);
             mbar_init(&bars[EB_XCHG + s], 1);
         }
-        mbar_init(&bars[EB_GFULL], 8);
+        mbar_init(&bars[EB_GFULL], GLO ? 4 : 8);   // BF16X2: the four warps of lane quadrants 0-1
+        if (GLO) {
+            mbar_init(&bars[EB_GFULL2], 4);
+            mbar_init(&bars[EB_GFREE2], 1);
+        }
         mbar_init(&bars[EB_GFREE], 1);
         mbar_init(&bars[EB_SDONE], 1);
         mbar_init(&bars[EB_TEMPTY], 8);
@@ -468,40 +480,69 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             if (w.first() && w.ui > 0) {   // the previous unit's accumulator has been written out
                 if (!mbar_wait(&bars[EB_TEMPTY], (w.ui - 1) & 1, abort_flag, p.err)) break;
             }
-            if (!mbar_wait(&bars[EB_GFULL], i & 1, abort_flag, p.err)) break;
-            tc_fence_after();
             const uint32_t sy = smem_u32(smem + L.y + (i % p.nstage) * L.y_stage);
-            if constexpr (SPARSE) {
-                if (w.first()) started = false;   // the next MMA initialises the unit's accumulator
-                for (int q = 0; q < kRows / 16; ++q) {
-                    // a K step whose 16 x 128 posteriors are all zero adds nothing;
-                    // a unit's last tile issues its first step regardless when
-                    // nothing was issued yet (zero posteriors then zero the accumulator)
-                    ++nsteps;
-                    if (!(flags[q] | flags[8 + q]) && (started || !w.last() || q > 0)) {
-                        ++nskip;
-                        continue;
+            if constexpr (GLO) {
+                // BF16X2: gamma^T hi + lo of rows 0-63, then of rows 64-127, through
+                // the same buffer (hi at sG, lo at sG + kGHalf, 64-component blocks
+                // kSub apart); each half has its own full / free barrier pair
+                if (SPARSE && w.first()) started = false;
+                bool ok = true;
+                for (int hf = 0; hf < 2; ++hf) {
+                    if (!mbar_wait(&bars[hf ? EB_GFULL2 : EB_GFULL], i & 1, abort_flag, p.err)) {
+                        ok = false;
+                        break;
                     }
-                    const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
-                    const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
-                    mma_bf16(tmem + kStatCol, a, b, idesc_s, started ? 1u : 0u);
-                    if constexpr (GLO)
-                        mma_bf16(tmem + kStatCol, sdesc_sw128(sG + 2 * kGHalf + q * 2048, kGHalf, 1024), b, idesc_s, 1u);
-                    started = true;
+                    tc_fence_after();
+                    for (int ql = 0; ql < 4; ++ql) {
+                        const int q = hf * 4 + ql;   // K step: rows 16q .. 16q + 15 of the tile
+                        if constexpr (SPARSE) {
+                            ++nsteps;
+                            if (!(flags[q] | flags[8 + q]) && (started || !w.last() || q > 0)) {
+                                ++nskip;
+                                continue;
+                            }
+                        }
+                        const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                        const uint32_t accum = SPARSE ? (started ? 1u : 0u) : ((w.first() && q == 0) ? 0u : 1u);
+                        mma_bf16(tmem + kStatCol, sdesc_sw128(sG + ql * 2048, kSub, 1024), b, idesc_s, accum);
+                        mma_bf16(tmem + kStatCol, sdesc_sw128(sG + kGHalf + ql * 2048, kSub, 1024), b, idesc_s, 1u);
+                        started = true;
+                    }
+                    mma_commit(&bars[hf ? EB_GFREE2 : EB_GFREE]);
+                    issued = true;   // drained before TMEM is freed, even if the next wait gives up
                 }
+                if (!ok) break;
             } else {
-                for (int q = 0; q < kRows / 16; ++q) {
-                    // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
-                    // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
-                    // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
-                    const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
-                    const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
-                    mma_bf16(tmem + kStatCol, a, b, idesc_s, (w.first() && q == 0) ? 0u : 1u);
-                    if constexpr (GLO)   // the lo halves of the posteriors, same Y planes
-                        mma_bf16(tmem + kStatCol, sdesc_sw128(sG + 2 * kGHalf + q * 2048, kGHalf, 1024), b, idesc_s, 1u);
+                if (!mbar_wait(&bars[EB_GFULL], i & 1, abort_flag, p.err)) break;
+                tc_fence_after();
+                if constexpr (SPARSE) {
+                    if (w.first()) started = false;   // the next MMA initialises the unit's accumulator
+                    for (int q = 0; q < kRows / 16; ++q) {
+                        // a K step whose 16 x 128 posteriors are all zero adds nothing;
+                        // a unit's last tile issues its first step regardless when
+                        // nothing was issued yet (zero posteriors then zero the accumulator)
+                        ++nsteps;
+                        if (!(flags[q] | flags[8 + q]) && (started || !w.last() || q > 0)) {
+                            ++nskip;
+                            continue;
+                        }
+                        const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
+                        const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                        mma_bf16(tmem + kStatCol, a, b, idesc_s, started ? 1u : 0u);
+                        started = true;
+                    }
+                } else {
+                    for (int q = 0; q < kRows / 16; ++q) {
+                        // gamma^T: MN-major, 128-byte swizzle, 64-component halves kGHalf
+                        // apart, 8-row groups 1 KB apart; Y: MN-major, 16-column blocks
+                        // kBlk apart, 8-row groups 256 B apart; 16 rows per K step
+                        const uint64_t a = sdesc_sw128(sG + q * 2048, kGHalf, 1024);
+                        const uint64_t b = sdesc_sw32(sy + q * 512, kBlk, 256);
+                        mma_bf16(tmem + kStatCol, a, b, idesc_s, (w.first() && q == 0) ? 0u : 1u);
+                    }
                 }
+                mma_commit(&bars[EB_GFREE]);
             }
-            mma_commit(&bars[EB_GFREE]);
             mma_commit(&bars[EB_STFREE + (i & 1)]);
             if (w.last()) mma_commit(&bars[EB_SDONE]);
             issued = true;
@@ -550,7 +591,9 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         const float *cl = reinterpret_cast<const float *>(smem + L.cl) + h * 64;
         float2 *xbuf = reinterpret_cast<float2 *>(smem + L.xchg);
         float2 *hx = reinterpret_cast<float2 *>(smem + L.hx);
-        uint8_t *gsm = smem + L.g + h * kGHalf + r * 128;   // this row of this warp's 64-component half
+        // this row of this warp's 64-component half (BF16X2: of the 64-row half
+        // that holds it, hi here and lo kGHalf further)
+        uint8_t *gsm = GLO ? smem + L.g + h * kSub + (r & 63) * 128 : smem + L.g + h * kGHalf + r * 128;
         const int sw = r & 7;                  // 128-byte swizzle: 16-byte chunk j sits at j ^ (row & 7)
         int i = 0;
         TileWalk w(p.units, cu);
@@ -681,10 +724,28 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             }
             const float Mref = (M == -INFINITY) ? 0.f : M;
             const float inv = 1.0f / Z;
-            // the statistics GEMM of the previous tile has read gamma^T (these
-            // warps wait on every phase of GFREE in order, so none is skipped)
-            if (i >= 1 &&
-                !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], (i - 1) & 1, abort_flag, p.err))) break;
+            if constexpr (GLO) {
+                // BF16X2: rows 0-63 (quadrants 0-1) go into the buffer once the
+                // statistics GEMM has read rows 64-127 of the previous tile (and,
+                // at a unit's first tile, once the previous unit's write-out,
+                // which stages through this buffer, is over); rows 64-127 once
+                // it has read rows 0-63 of this tile. Every phase is waited on.
+                if (q < 2) {
+                    if (w.first() && w.ui > 0 &&
+                        !__all_sync(0xffffffffu, mbar_wait(&bars[EB_TEMPTY], (w.ui - 1) & 1, abort_flag, p.err)))
+                        break;
+                    if (i >= 1 &&
+                        !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE2], (i - 1) & 1, abort_flag, p.err)))
+                        break;
+                } else if (!__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], i & 1, abort_flag, p.err))) {
+                    break;
+                }
+            } else {
+                // the statistics GEMM of the previous tile has read gamma^T (these
+                // warps wait on every phase of GFREE in order, so none is skipped)
+                if (i >= 1 &&
+                    !__all_sync(0xffffffffu, mbar_wait(&bars[EB_GFREE], (i - 1) & 1, abort_flag, p.err))) break;
+            }
             // pass B: normalised posteriors -> bf16 gamma^T from the registers of pass A
             bool row_nz = false;   // early termination: a posterior of this row and half above tau
 #pragma unroll
@@ -714,7 +775,7 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                             lv[e] = pack_bf16x2(g0 - h0, g1 - h1);
                         }
                         *reinterpret_cast<uint4 *>(gsm + (((c * 4 + k) ^ sw) << 4)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *reinterpret_cast<uint4 *>(gsm + 2 * kGHalf + (((c * 4 + k) ^ sw) << 4)) =
+                        *reinterpret_cast<uint4 *>(gsm + kGHalf + (((c * 4 + k) ^ sw) << 4)) =
                             make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     } else {
                         uint4 v;
@@ -735,7 +796,7 @@ bf16_encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
             }
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bars[EB_GFULL]);
+            if (lane == 0) mbar_arrive(&bars[GLO && q >= 2 ? EB_GFULL2 : EB_GFULL]);
             const bool last = w.last();
             const int uidx = w.ui, uslot = w.slot();
             w.next();

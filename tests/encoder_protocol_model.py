@@ -13,6 +13,11 @@ log-likelihood buffer, gamma^T, statistics accumulator, exchange slot) is
 overwritten while in use or read before it holds the right tile, and that the
 run neither deadlocks nor loses a unit's statistics.
 
+glo=True models FV_PREC_BF16X2: the posteriors' bf16 hi + lo pair of a tile
+goes through the gamma^T buffer in two 64-row halves (lane quadrants 0-1,
+then 2-3), each with its own full / free barrier, and the statistics
+write-out's staging shares the buffer with the next unit's first half.
+
 This is test infrastructure: nothing in the library imports it.
 """
 import random
@@ -38,7 +43,7 @@ class Fail(Exception): pass
 def check(c, msg):
     if not c: raise Fail(msg)
 
-def run(units_per_cluster, S, nstage, seed, drop=frozenset()):
+def run(units_per_cluster, S, nstage, seed, drop=frozenset(), glo=False):
     rng = random.Random(seed)
     tiles = []
     for ui, n in enumerate(units_per_cluster):
@@ -57,8 +62,12 @@ def run(units_per_cluster, S, nstage, seed, drop=frozenset()):
             mk(f'LEMPTY{s}', 8); mk(f'XCHG{s}', 1)
         for q in range(4):
             mk(f'HXFULL{q}', 2); mk(f'HXFREE{q}', 2)   # two warps per quadrant (one arrival each here)
-        mk('GFULL', 8); mk('GFREE', 1); mk('SDONE', 1); mk('TEMPTY', 8)
-        st = dict(ring=None, stage=[[None] * 6 for _ in range(2)], L=[None, None], gam=[None] * 8,
+        mk('GFULL', 4 if glo else 8); mk('GFREE', 1); mk('SDONE', 1); mk('TEMPTY', 8)
+        if glo:
+            mk('GFULL2', 4); mk('GFREE2', 1)
+        # gamma^T buffer as eight 4 KB units -> [tile, half, consumed]; stg: the write-out staging owner
+        st = dict(ring=None, stage=[[None] * 6 for _ in range(2)], L=[None, None],
+                  gbuf={k: None for k in range(8)}, stg={k: None for k in range(8)},
                   acc=None, xbuf=[[[None] * 4 for _ in range(S)] for _ in range(2)], hx=[[None, None] for _ in range(4)],
                   flushed=[])
         ctas.append(dict(B=B, st=st, mmaq=[], mmaq2=[], tmaq=[]))
@@ -124,18 +133,24 @@ def run(units_per_cluster, S, nstage, seed, drop=frozenset()):
             ui, first, last = tiles[ns]
             if first and ui > 0 and 'stats_tempty' not in drop:
                 yield ('wait', B['TEMPTY'], (ui - 1) & 1)
-            yield ('wait', B['GFULL'], ns & 1)
             s = ns % nstage
-            def op(ti=ns, s=s, ui=ui, first=first):
-                check(all(x == ti for x in st['stage'][s]), f'stats {ti} stage {st["stage"][s]}')
-                check(all(x == ti for x in st['gam']), f'stats {ti} gamma {st["gam"]}')
-                if first:
-                    check(st['acc'] is None or st['acc'][2], f'acc overwritten before flush {st["acc"]}')
-                    st['acc'] = [ui, 1, False]
-                else:
-                    check(st['acc'][0] == ui, 'acc unit')
-            q.append(('op', op))
-            q.append(('commit', B['GFREE']))
+            for half in ((0, 1) if glo else (0,)):
+                full = 'GFULL2' if half else 'GFULL'
+                yield ('wait', B[full], ns & 1)
+                def op(ti=ns, s=s, ui=ui, first=first, half=half):
+                    check(all(x == ti for x in st['stage'][s]), f'stats {ti} stage {st["stage"][s]}')
+                    check(all(v is not None and v[0] == ti and v[1] == half for v in st['gbuf'].values()),
+                          f'stats {ti}/{half} gamma {st["gbuf"]}')
+                    check(all(o is None for o in st['stg'].values()), f'stats {ti} gamma under staging {st["stg"]}')
+                    for v in st['gbuf'].values():
+                        v[2] = True
+                    if first and half == 0:
+                        check(st['acc'] is None or st['acc'][2], f'acc overwritten before flush {st["acc"]}')
+                        st['acc'] = [ui, 1, False]
+                    else:
+                        check(st['acc'][0] == ui, 'acc unit')
+                q.append(('op', op))
+                q.append(('commit', B['GFREE2' if half else 'GFREE']))
             q.append(('commit', B[f'STFREE{ns & 1}']))
             if last:
                 def mark(ui=ui): st['acc_done'] = ui
@@ -186,17 +201,36 @@ def run(units_per_cluster, S, nstage, seed, drop=frozenset()):
                 for pr in range(S):
                     if pr != rank:
                         check(st['xbuf'][j][pr][q] == i, f'xchg {i} changed')
-            if i >= 1 and 'softmax_gfree' not in drop:
-                yield ('wait', B['GFREE'], (i - 1) & 1)
-            st['gam'][wid] = i
-            yield ('step',)
-            B['GFULL'].arrive()
             ui, first, last = tiles[i]
+            half = (q >> 1) if glo else 0
+            # pass B writes: BF16 its 32 rows of component half h (unit 4h + q); BF16X2 its rows of the
+            # 64-row half, hi at unit 2h + (q & 1) and lo at 4 + 2h + (q & 1); the staging uses unit 4h + q
+            units = [2 * h + (q & 1), 4 + 2 * h + (q & 1)] if glo else [4 * h + q]
+            slot = 4 * h + q
+            if glo and half == 0 and first and ui > 0 and 'softmax_tempty' not in drop:
+                yield ('wait', B['TEMPTY'], (ui - 1) & 1)   # the staging in this buffer is over
+            if 'softmax_gfree' not in drop:
+                if half == 0 and i >= 1:
+                    yield ('wait', B['GFREE2' if glo else 'GFREE'], (i - 1) & 1)
+                elif half == 1:
+                    yield ('wait', B['GFREE'], i & 1)
+            for u in units:
+                check(st['stg'][u] is None, f'pass B {i} writes rows under staging {st["stg"]}')
+                check(st['gbuf'][u] is None or st['gbuf'][u][2], f'pass B {i} overwrites unread gamma {st["gbuf"][u]}')
+                st['gbuf'][u] = [i, half, False]
+            yield ('step',)
+            B['GFULL2' if half else 'GFULL'].arrive()
             if not last: continue
             yield ('wait', B['SDONE'], ui & 1)
             check(st.get('acc_done') == ui and st['acc'][0] == ui, f'flush {ui} acc {st["acc"]}')
+            # the write-out stages through this warp's slot of the gamma^T buffer
+            check(st['stg'][slot] is None and (st['gbuf'][slot] is None or st['gbuf'][slot][2]),
+                  f'staging {ui} over unread gamma {st["gbuf"][slot]} / {st["stg"][slot]}')
+            st['stg'][slot] = wid
             yield ('step',)
             check(st['acc'][0] == ui, 'acc changed during flush')
+            check(st['stg'][slot] == wid, f'staging {ui} disturbed')
+            st['stg'][slot] = None
             if B['TEMPTY'].pending == 1:
                 st['acc'][2] = True
                 st['flushed'].append(ui)
