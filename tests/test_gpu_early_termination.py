@@ -75,12 +75,15 @@ def test_bf16_threshold_mode_matches_oracle(K, D, N, seed):
     assert 0 <= skipped <= visited and visited > 0
 
 
-def test_bf16_block_skips_on_sorted_descriptors_and_all_skipped_units():
+@pytest.mark.parametrize("prec", [fv.FV_PREC_BF16, fv.FV_PREC_BF16X2])
+def test_bf16_block_skips_on_sorted_descriptors_and_all_skipped_units(prec):
     """Descriptors ordered by their generating component put many 16-row K
     steps entirely on one CTA's components, so the other CTA skips them; a
     frame drawn only from components 0-127 (components 128-255 far away)
     leaves the second CTA no posterior above tau in any K step, which must
-    still give exact zeros for those components' statistics."""
+    still give exact zeros for those components' statistics. Both BF16
+    forms (the hi + lo posteriors go through the statistics GEMM in two
+    64-row halves)."""
     K, D = 256, 32
     w, mu, var = synth.make_gmm(K, D, seed=68)
     mu = mu.copy()
@@ -91,12 +94,12 @@ def test_bf16_block_skips_on_sorted_descriptors_and_all_skipped_units():
     comp2 = np.sort(g.choice(K, size=6000, p=w / w.sum()))
     X2 = (mu[comp2] + np.sqrt(var[comp2]) * g.standard_normal((6000, D))).astype(np.float32)
     X = np.concatenate([X1, X2])
-    st, out, (skipped, visited) = _run(fv.FV_PREC_BF16, X, w, mu, var, TAU, offsets=[0, 6000, 12000])
+    st, out, (skipped, visited) = _run(prec, X, w, mu, var, TAU, offsets=[0, 6000, 12000])
     assert st == fv.FV_OK
     assert skipped > visited // 4, (skipped, visited)
     for f, Xf in enumerate((X1, X2)):
         ref = _ref(synth.to_bf16_grid(Xf), w, mu, var, TAU)
-        assert max_err(out[f], ref) <= TOL[fv.FV_PREC_BF16]
+        assert max_err(out[f], ref) <= TOL[prec]
     # the first frame's components 128..255 have no posterior above tau: zero blocks
     KD = K * D
     assert np.all(out[0][128 * D:KD] == 0) and np.all(out[0][KD + 128 * D:] == 0)
