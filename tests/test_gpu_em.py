@@ -33,7 +33,8 @@ def _check(got, ref, var_ref, mu_old, reg):
 
 
 @pytest.mark.parametrize("K,D,N,seed,on_device", [(64, 32, 5000, 81, True), (256, 64, 19200, 82, False),
-                                                 (7, 5, 333, 83, True), (130, 17, 2000, 84, False)])
+                                                 (7, 5, 333, 83, True), (130, 17, 2000, 84, False),
+                                                 (512, 64, 8000, 85, True)])   # the largest component count
 def test_em_step_matches_oracle(K, D, N, seed, on_device):
     torch = torch_cuda()
     X, w, mu, var = case(K, D, N, seed)
