@@ -302,14 +302,15 @@ FV_API int fv_gmm_fit(const fv_gmm_desc *init, const float *X, int64_t N, int x_
 
 /* ---- batched form: one CUDA-graph launch per batch ---------------------------
  * A plan owns every device buffer a batch of up to max_frames frames and
- * max_rows descriptors needs (bfloat16 input rows, posteriors, statistics
- * slots, work lists, output vectors) and a CUDA graph of the whole kernel
- * sequence (posteriors, statistics, finalise), captured once against those
- * buffers. The kernels read the batch's row and frame counts from device
+ * max_rows descriptors needs (bfloat16 input rows, statistics slots, work
+ * lists, output vectors; the fused encoder keeps the posteriors on chip) and
+ * a CUDA graph of the whole kernel sequence (fused posteriors + statistics,
+ * slot reduction, finalise), captured once against those buffers. The kernels read the batch's row and frame counts from device
  * memory, so a run uploads one small work list and launches the graph once:
  * frames of uneven size share the persistent kernels (Algorithm 1 for every
  * frame; the per-block copies and reduction of Algorithm 3 become per-share
- * statistics slots reduced per frame). FV_PREC_BF16 handles only.
+ * statistics slots reduced per frame). FV_PREC_BF16 and FV_PREC_BF16X2
+ * handles only.
  *
  * The tile pipeline is chosen by a measured autotune at creation (when
  * requested): every pair of Y-stage count (1, or 2 where two fit shared
@@ -426,7 +427,7 @@ FV_API void fv_server_destroy(fv_server *srv);
  *   X        N x D float32 row-major descriptors, DEVICE memory,
  *   fv_out   2*K*D float32, DEVICE memory.
  * The scratch needs about N*Kp*4 bytes for the posteriors (Kp = K rounded up
- * to 64) plus the per-range statistics; larger inputs are rejected with
+ * to 64), N*4 bytes of posterior group masks, plus the per-range statistics; larger inputs are rejected with
  * FV_ERR_UNSUPPORTED and a message giving the limit (e.g. N=19200, K=256,
  * D=64 fits). The first call on a device looks up the array's device address
  * (make that first call before any stream capture). All calls share the

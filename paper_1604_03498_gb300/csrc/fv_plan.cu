@@ -223,7 +223,7 @@ extern "C" int fv_batch_plan_create(const fv_gmm *gmm, const fv_batch_plan_confi
     if (!out) return fail(FV_ERR_INVALID, "fv_batch_plan_create: out is NULL");
     *out = nullptr;
     if (!gmm || !cfg) return fail(FV_ERR_INVALID, "fv_batch_plan_create: NULL GMM or config");
-    if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_batch_plan_create: needs an FV_PREC_BF16 GMM");
+    if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_batch_plan_create: needs an FV_PREC_BF16 or FV_PREC_BF16X2 GMM");
     if (cfg->max_frames < 1 || cfg->max_rows < 1) return fail(FV_ERR_INVALID, "fv_batch_plan_create: empty capacity");
     if (cfg->max_rows > (int64_t)INT32_MAX - 256)
         return fail(FV_ERR_UNSUPPORTED, "fv_batch_plan_create: max_rows beyond 2^31 - 256");
