@@ -398,7 +398,7 @@ extern "C" int fv_encode_batch_bf16(const fv_gmm *gmm, const uint16_t *X_bf16, i
                                     int B, float *fv_out, void *cuda_stream) {
     int rc = check_common(gmm, fv_out);
     if (rc != FV_OK) return rc;
-    if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_encode_batch_bf16 needs an FV_PREC_BF16 GMM");
+    if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_encode_batch_bf16 needs an FV_PREC_BF16 or FV_PREC_BF16X2 GMM");
     if (B <= 0 || !offsets) return fail(FV_ERR_INVALID, "B must be > 0 and offsets non-NULL");
     if (ld_x < gmm->D || ld_x % 8 != 0) return fail(FV_ERR_INVALID, "ld_x must be >= D and a multiple of 8");
     if (((uintptr_t)X_bf16) % 16 != 0) return fail(FV_ERR_INVALID, "X_bf16 must be 16-byte aligned");

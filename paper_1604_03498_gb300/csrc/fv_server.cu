@@ -278,7 +278,7 @@ extern "C" int fv_server_create(const fv_gmm *gmm, const fv_server_config *cfg, 
     if (!out) return fail(FV_ERR_INVALID, "fv_server_create: out is NULL");
     *out = nullptr;
     if (!gmm || !cfg) return fail(FV_ERR_INVALID, "fv_server_create: NULL GMM or config");
-    if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_server_create: needs an FV_PREC_BF16 GMM");
+    if (!is_bf16(gmm->prec)) return fail(FV_ERR_INVALID, "fv_server_create: needs an FV_PREC_BF16 or FV_PREC_BF16X2 GMM");
     if (cfg->max_slots < 1 || cfg->hbm_budget_bytes <= 0 || cfg->max_batch_frames < 1 ||
         cfg->max_batch_frames > 65535 ||
         cfg->max_frame_descriptors < 1 || cfg->max_batch_descriptors < cfg->max_frame_descriptors)
