@@ -24,8 +24,12 @@
 //   kernel 2 computes, for every row and lattice column only, the gradients of
 //            the 2b - 1 pixels around it, their orientation split and the
 //            x-pass sum (8 channels),
-//   kernel 3 gives one warp to a descriptor: each lane forms 4 of the 128
-//            entries as y-pass sums over the lattice rows, then the warp
+//   kernel 3 computes the y-pass once at every lattice point (row
+//            b/2 + S m, column b/2 + S t), the 8 channels' sums over the
+//            2b - 1 rows around it (a bin centre is shared by up to 16
+//            descriptors),
+//   kernel 4 gives one warp to a descriptor: each lane reads 4 of the 128
+//            entries (one 16-byte load from the y-pass buffer), then the warp
 //            normalises.
 #include <cmath>
 #include <string>
@@ -43,8 +47,11 @@ struct DsScale {
     float inv_s;      // 1 / s
     int ny, nx;       // descriptor grid
     int Tx;           // lattice columns b/2 + S t, t < Tx
+    int Ty;           // lattice rows b/2 + S m, m < Ty
     int64_t img_off;  // floats into a frame's pyramid
     int64_t tmp_off;  // floats into a frame's x-pass buffer [8][Hs][Tx]
+    int64_t yp_off;   // floats into a frame's y-pass buffer [Ty][Tx][8]
+    int64_t lat_off;  // first y-pass thread (lattice point) of the scale within a frame
     int64_t desc_off; // first descriptor of the scale within a frame
     int64_t pix_off;  // first x-pass thread of the scale within a frame
 };
@@ -53,6 +60,7 @@ struct DsPlan {
     int n, b, S;
     DsScale s[kMaxScales];
     int64_t pyr, tmp, ndesc, npix;   // per-frame totals (pyramid floats, x-pass floats, descriptors, x-pass points)
+    int64_t yp, nlat;                // per-frame totals (y-pass floats, lattice points)
 };
 
 int plan_dsift(int H, int W, const fv_dsift_params *prm, DsPlan &p) {
@@ -67,7 +75,7 @@ int plan_dsift(int H, int W, const fv_dsift_params *prm, DsPlan &p) {
     p.n = d.n_scales;
     p.b = d.bin_size;
     p.S = d.stride;
-    p.pyr = p.tmp = p.ndesc = p.npix = 0;
+    p.pyr = p.tmp = p.ndesc = p.npix = p.yp = p.nlat = 0;
     for (int j = 0; j < p.n; ++j) {
         const double s = std::pow(2.0, (d.top_scale - j) / 2.0);
         DsScale &c = p.s[j];
@@ -78,24 +86,21 @@ int plan_dsift(int H, int W, const fv_dsift_params *prm, DsPlan &p) {
         c.ny = c.Hs - 2 * p.b >= 2 * p.b ? (c.Hs - 4 * p.b) / p.S + 1 : 0;
         if (c.nx == 0 || c.ny == 0) c.nx = c.ny = 0;
         c.Tx = c.nx > 0 ? c.nx + 3 * p.b / p.S : 0;
+        c.Ty = c.ny > 0 ? c.ny + 3 * p.b / p.S : 0;
         c.img_off = p.pyr;
         c.tmp_off = p.tmp;
         c.desc_off = p.ndesc;
         c.pix_off = p.npix;
+        c.yp_off = p.yp;
+        c.lat_off = p.nlat;
         p.pyr += (int64_t)c.Hs * c.Ws;
         p.tmp += (int64_t)8 * c.Hs * c.Tx;
         p.ndesc += (int64_t)c.ny * c.nx;
         p.npix += (int64_t)c.Hs * c.Tx;
+        p.yp += (int64_t)8 * c.Ty * c.Tx;
+        p.nlat += (int64_t)c.Ty * c.Tx;
     }
     return FV_OK;
-}
-
-__device__ __forceinline__ int find_scale(const DsPlan &p, int64_t i, bool pix) {
-    int j = 0;
-#pragma unroll 1
-    for (int q = 1; q < p.n; ++q)
-        if (i >= (pix ? p.s[q].pix_off : p.s[q].img_off)) j = q;
-    return j;
 }
 
 // grid (ceil(pyr / 256), B): every pixel of every scale of every frame.
@@ -172,9 +177,40 @@ dsift_xpass_kernel(const float *__restrict__ pyr, DsPlan p, float *__restrict__ 
     for (int o = 0; o < 8; ++o) out[(size_t)o * Hs * c.Tx] = acc[o];
 }
 
+// grid (ceil(nlat / 256), B): y-pass at every lattice point (m, t), all 8
+// channels, the taps in the same order as a per-descriptor sum would take them.
+__global__ void __launch_bounds__(256)
+dsift_ypass_kernel(const float *__restrict__ tmp, DsPlan p, float *__restrict__ yp) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= p.nlat) return;
+    const int f = blockIdx.y;
+    int j = 0;
+#pragma unroll 1
+    for (int q = 1; q < p.n; ++q)
+        if (i >= p.s[q].lat_off) j = q;
+    const DsScale &c = p.s[j];
+    const int64_t k = i - c.lat_off;
+    const int m = (int)(k / c.Tx), t = (int)(k - (int64_t)m * c.Tx);
+    const int b = p.b, cy = b / 2 + p.S * m;
+    const float *src = tmp + (size_t)f * p.tmp + c.tmp_off + t;
+    float v[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) v[o] = 0.f;
+    for (int d = -(b - 1); d <= b - 1; ++d) {
+        const int y = cy + d;
+        if (y < 0 || y >= c.Hs) continue;
+        const float kw = 1.f - fabsf((float)d) / (float)b;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) v[o] = fmaf(kw, src[((size_t)o * c.Hs + y) * c.Tx], v[o]);
+    }
+    float4 *out = reinterpret_cast<float4 *>(yp + (size_t)f * p.yp + c.yp_off + (size_t)k * 8);
+    out[0] = make_float4(v[0], v[1], v[2], v[3]);
+    out[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
 // grid (ceil(ndesc / 8), B), block 256: one warp per descriptor.
 __global__ void __launch_bounds__(256)
-dsift_desc_kernel(const float *__restrict__ tmp, DsPlan p, float *__restrict__ desc, float *__restrict__ xy) {
+dsift_desc_kernel(const float *__restrict__ yp, DsPlan p, float *__restrict__ desc, float *__restrict__ xy) {
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= p.ndesc) return;
@@ -188,17 +224,10 @@ dsift_desc_kernel(const float *__restrict__ tmp, DsPlan p, float *__restrict__ d
     const int iy = (int)(k / c.nx), ix = (int)(k - (int64_t)iy * c.nx);
     const int b = p.b, bs = b / p.S;
     const int bin = lane >> 1, by = bin >> 2, bx = bin & 3, o0 = (lane & 1) * 4;
-    const int t = ix + bx * bs;                     // lattice column of this bin
-    const int cy = b / 2 + p.S * iy + by * b;       // row of this bin's centre
-    const float *src = tmp + (size_t)f * p.tmp + c.tmp_off + t;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int d = -(b - 1); d <= b - 1; ++d) {
-        const int y = cy + d;
-        if (y < 0 || y >= c.Hs) continue;
-        const float kw = 1.f - fabsf((float)d) / (float)b;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = fmaf(kw, src[((size_t)(o0 + e) * c.Hs + y) * c.Tx], v[e]);
-    }
+    // the bin's centre (x0 + (bx - 1.5) b, y0 + (by - 1.5) b) is lattice point (iy + by bs, ix + bx bs)
+    const int m = iy + by * bs, t = ix + bx * bs;
+    const float4 w4 = *reinterpret_cast<const float4 *>(yp + (size_t)f * p.yp + c.yp_off + ((size_t)m * c.Tx + t) * 8 + o0);
+    float v[4] = {w4.x, w4.y, w4.z, w4.w};
     float ss = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -231,14 +260,16 @@ bool dev_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// The three kernels over B device frames into device desc / xy.
+// The four kernels over B device frames into device desc / xy.
 int run_dsift(const float *img, int B, int H, int W, const DsPlan &p, float *desc, float *xy, cudaStream_t st) {
     if (p.ndesc == 0) return FV_OK;
     float *buf = nullptr;
-    const size_t bytes = sizeof(float) * (size_t)B * (p.pyr + p.tmp);
+    const size_t bytes = sizeof(float) * (size_t)B * (p.pyr + p.tmp + p.yp + 4);
     cudaError_t e = cudaMallocAsync((void **)&buf, bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "dense SIFT: cudaMallocAsync(scratch)");
     float *pyr = buf, *tmp = buf + (size_t)B * p.pyr;
+    // the y-pass buffer is read in 16-byte pieces: start it on a 16-byte boundary
+    float *yp = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tmp + (size_t)B * p.tmp) + 15) & ~uintptr_t(15));
     {
         KernelTimer kt_("dsift_resize", st);
         dsift_resize_kernel<<<dim3((unsigned)((p.pyr + 255) / 256), (unsigned)B), 256, 0, st>>>(img, H, W, p, pyr);
@@ -249,8 +280,13 @@ int run_dsift(const float *img, int B, int H, int W, const DsPlan &p, float *des
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
+        KernelTimer kt_("dsift_ypass", st);
+        dsift_ypass_kernel<<<dim3((unsigned)((p.nlat + 255) / 256), (unsigned)B), 256, 0, st>>>(tmp, p, yp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
         KernelTimer kt_("dsift_desc", st);
-        dsift_desc_kernel<<<dim3((unsigned)((p.ndesc + 7) / 8), (unsigned)B), 256, 0, st>>>(tmp, p, desc, xy);
+        dsift_desc_kernel<<<dim3((unsigned)((p.ndesc + 7) / 8), (unsigned)B), 256, 0, st>>>(yp, p, desc, xy);
         e = cudaGetLastError();
     }
     cudaFreeAsync(buf, st);
