@@ -427,9 +427,12 @@ extern "C" int fv_encode_batch_opts(const fv_gmm *gmm, const void *X, int x_is_b
                        tau, cnt);
 }
 
-extern "C" int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *X, const float *xy,
-                             const int64_t *offsets, int B, int x_on_device, float *fv_out, int out_on_device,
-                             void *cuda_stream) {
+namespace fv {
+// fv_encode_pca with the rows either read from X or (yp != nullptr, device
+// memory, BF16 form) assembled from a dense-SIFT y-pass buffer.
+int encode_pca_impl(const fv_gmm *gmm, const fv_pca *pca, const float *X, const float *xy, const int64_t *offsets,
+                    int B, int x_on_device, float *fv_out, int out_on_device, void *cuda_stream, const float *yp,
+                    const DsPlan *dsp) {
     int rc = check_common(gmm, fv_out);
     if (rc != FV_OK) return rc;
     if (!pca) return fail(FV_ERR_INVALID, "fv_encode_pca: NULL PCA handle");
@@ -442,9 +445,13 @@ extern "C" int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *
     for (int b = 0; b < B; ++b)
         if (offsets[b + 1] < offsets[b]) return fail(FV_ERR_INVALID, "offsets must be non-decreasing");
     const int64_t N = offsets[B];
-    if (N > 0 && !X) return fail(FV_ERR_INVALID, "descriptor pointer is NULL");
-    if (x_on_device && N > 0 && (!is_device_ptr(X) || (xy && !is_device_ptr(xy))))
-        return fail(FV_ERR_INVALID, "x_on_device=1 but X or xy is not device memory");
+    if (yp) {
+        if (!is_bf16(gmm->prec) || !x_on_device) return fail(FV_ERR_INVALID, "fv_encode_pca: gather needs the BF16 form");
+    } else {
+        if (N > 0 && !X) return fail(FV_ERR_INVALID, "descriptor pointer is NULL");
+        if (x_on_device && N > 0 && (!is_device_ptr(X) || (xy && !is_device_ptr(xy))))
+            return fail(FV_ERR_INVALID, "x_on_device=1 but X or xy is not device memory");
+    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool bf16 = is_bf16(gmm->prec);
     const int D = gmm->D, ld = bf16 ? gmm->Dp : D;
@@ -474,11 +481,11 @@ extern "C" int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *
             Xd = (const float *)(s.base + o_x);
             xyd = xy ? (const float *)(s.base + o_xy) : nullptr;
         }
-        if (N > 0 && ((uintptr_t)Xd) % 16 != 0) {
+        if (!yp && N > 0 && ((uintptr_t)Xd) % 16 != 0) {
             rc = fail(FV_ERR_INVALID, "fv_encode_pca: X must be 16-byte aligned");
             break;
         }
-        if ((e = launch_pca(pca, Xd, xyd, N, bf16, s.base + o_y, ld, errd, st)) != cudaSuccess) {
+        if ((e = launch_pca(pca, Xd, xyd, N, bf16, s.base + o_y, ld, errd, st, yp, dsp)) != cudaSuccess) {
             rc = cuda_fail(e, "fv_encode_pca: projection launch");
             break;
         }
@@ -495,6 +502,14 @@ extern "C" int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *
     } while (0);
     cudaFreeAsync(s.base, st);
     return rc;
+}
+}  // namespace fv
+
+extern "C" int fv_encode_pca(const fv_gmm *gmm, const fv_pca *pca, const float *X, const float *xy,
+                             const int64_t *offsets, int B, int x_on_device, float *fv_out, int out_on_device,
+                             void *cuda_stream) {
+    return encode_pca_impl(gmm, pca, X, xy, offsets, B, x_on_device, fv_out, out_on_device, cuda_stream, nullptr,
+                           nullptr);
 }
 
 // ---- instrumentation ------------------------------------------------------------

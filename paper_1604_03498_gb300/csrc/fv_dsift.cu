@@ -31,37 +31,18 @@
 //   kernel 4 gives one warp to a descriptor: each lane reads 4 of the 128
 //            entries (one 16-byte load from the y-pass buffer), then the warp
 //            normalises.
+// fv_encode_images in the BF16 form skips kernel 4: the PCA projection reads
+// each descriptor's 16 bins from the y-pass buffer and normalises them itself,
+// so the FP32 descriptors are never written out.
 #include <cmath>
 #include <string>
 #include <vector>
 
+#include "fv_dsift.h"
 #include "fv_internal.h"
 
 namespace fv {
 namespace {
-
-constexpr int kMaxScales = 9;
-
-struct DsScale {
-    int Hs, Ws;
-    float inv_s;      // 1 / s
-    int ny, nx;       // descriptor grid
-    int Tx;           // lattice columns b/2 + S t, t < Tx
-    int Ty;           // lattice rows b/2 + S m, m < Ty
-    int64_t img_off;  // floats into a frame's pyramid
-    int64_t tmp_off;  // floats into a frame's x-pass buffer [8][Hs][Tx]
-    int64_t yp_off;   // floats into a frame's y-pass buffer [Ty][Tx][8]
-    int64_t lat_off;  // first y-pass thread (lattice point) of the scale within a frame
-    int64_t desc_off; // first descriptor of the scale within a frame
-    int64_t pix_off;  // first x-pass thread of the scale within a frame
-};
-
-struct DsPlan {
-    int n, b, S;
-    DsScale s[kMaxScales];
-    int64_t pyr, tmp, ndesc, npix;   // per-frame totals (pyramid floats, x-pass floats, descriptors, x-pass points)
-    int64_t yp, nlat;                // per-frame totals (y-pass floats, lattice points)
-};
 
 int plan_dsift(int H, int W, const fv_dsift_params *prm, DsPlan &p) {
     fv_dsift_params d{4, 4, 8, 1};
@@ -251,6 +232,26 @@ dsift_desc_kernel(const float *__restrict__ yp, DsPlan p, float *__restrict__ de
     }
 }
 
+// grid (ceil(ndesc / 256), B): positions only (the fused images path, whose
+// descriptors are assembled inside the PCA projection).
+__global__ void __launch_bounds__(256)
+dsift_xy_kernel(DsPlan p, float *__restrict__ xy) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= p.ndesc) return;
+    const int f = blockIdx.y;
+    int j = 0;
+#pragma unroll 1
+    for (int q = 1; q < p.n; ++q)
+        if (i >= p.s[q].desc_off) j = q;
+    const DsScale &c = p.s[j];
+    const int64_t k = i - c.desc_off;
+    const int iy = (int)(k / c.nx), ix = (int)(k - (int64_t)iy * c.nx);
+    const int x0 = 2 * p.b + p.S * ix, y0 = 2 * p.b + p.S * iy;
+    const size_t row = (size_t)f * p.ndesc + i;
+    xy[row * 2] = (float)x0 / (float)c.Ws - 0.5f;
+    xy[row * 2 + 1] = (float)y0 / (float)c.Hs - 0.5f;
+}
+
 bool dev_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -260,21 +261,22 @@ bool dev_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// The four kernels over B device frames into device desc / xy.
-int run_dsift(const float *img, int B, int H, int W, const DsPlan &p, float *desc, float *xy, cudaStream_t st) {
-    if (p.ndesc == 0) return FV_OK;
-    float *buf = nullptr;
-    const size_t bytes = sizeof(float) * (size_t)B * (p.pyr + p.tmp + p.yp + 4);
-    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, st);
-    if (e != cudaSuccess) return cuda_fail(e, "dense SIFT: cudaMallocAsync(scratch)");
-    float *pyr = buf, *tmp = buf + (size_t)B * p.pyr;
-    // the y-pass buffer is read in 16-byte pieces: start it on a 16-byte boundary
-    float *yp = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tmp + (size_t)B * p.tmp) + 15) & ~uintptr_t(15));
+// Scratch of the lattice stages for B frames: pyramid, x-pass, y-pass (16-byte aligned).
+size_t lattice_floats(const DsPlan &p, int B) { return (size_t)B * (p.pyr + p.tmp + p.yp) + 4; }
+float *lattice_yp(float *buf, const DsPlan &p, int B) {
+    float *tmp_end = buf + (size_t)B * (p.pyr + p.tmp);
+    return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tmp_end) + 15) & ~uintptr_t(15));
+}
+
+// Resampling, x-pass and y-pass of B device frames into buf (lattice_floats floats).
+cudaError_t run_lattice(const float *img, int B, int H, int W, const DsPlan &p, float *buf, cudaStream_t st) {
+    float *pyr = buf, *tmp = buf + (size_t)B * p.pyr, *yp = lattice_yp(buf, p, B);
     {
         KernelTimer kt_("dsift_resize", st);
         dsift_resize_kernel<<<dim3((unsigned)((p.pyr + 255) / 256), (unsigned)B), 256, 0, st>>>(img, H, W, p, pyr);
     }
-    if ((e = cudaGetLastError()) == cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
         KernelTimer kt_("dsift_xpass", st);
         dsift_xpass_kernel<<<dim3((unsigned)((p.npix + 255) / 256), (unsigned)B), 256, 0, st>>>(pyr, p, tmp);
         e = cudaGetLastError();
@@ -284,9 +286,20 @@ int run_dsift(const float *img, int B, int H, int W, const DsPlan &p, float *des
         dsift_ypass_kernel<<<dim3((unsigned)((p.nlat + 255) / 256), (unsigned)B), 256, 0, st>>>(tmp, p, yp);
         e = cudaGetLastError();
     }
+    return e;
+}
+
+// The four kernels over B device frames into device desc / xy.
+int run_dsift(const float *img, int B, int H, int W, const DsPlan &p, float *desc, float *xy, cudaStream_t st) {
+    if (p.ndesc == 0) return FV_OK;
+    float *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, sizeof(float) * lattice_floats(p, B), st);
+    if (e != cudaSuccess) return cuda_fail(e, "dense SIFT: cudaMallocAsync(scratch)");
+    e = run_lattice(img, B, H, W, p, buf, st);
     if (e == cudaSuccess) {
         KernelTimer kt_("dsift_desc", st);
-        dsift_desc_kernel<<<dim3((unsigned)((p.ndesc + 7) / 8), (unsigned)B), 256, 0, st>>>(yp, p, desc, xy);
+        dsift_desc_kernel<<<dim3((unsigned)((p.ndesc + 7) / 8), (unsigned)B), 256, 0, st>>>(lattice_yp(buf, p, B), p,
+                                                                                           desc, xy);
         e = cudaGetLastError();
     }
     cudaFreeAsync(buf, st);
@@ -361,15 +374,37 @@ extern "C" int fv_encode_images(const fv_gmm *gmm, const fv_pca *pca, const floa
     float *owned = nullptr, *buf = nullptr;
     rc = stage_frames(images, B, H, W, images_on_device, st, &d, &owned);
     const size_t n = (size_t)B * p.ndesc;
-    if (rc == FV_OK) {
-        cudaError_t e = cudaMallocAsync((void **)&buf, sizeof(float) * n * 130, st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "fv_encode_images: cudaMallocAsync(descriptors)");
-    }
-    if (rc == FV_OK) rc = run_dsift(d, B, H, W, p, buf, buf + n * 128, st);
-    if (rc == FV_OK) {
-        std::vector<int64_t> offs(B + 1);
-        for (int b = 0; b <= B; ++b) offs[b] = (int64_t)b * p.ndesc;
-        rc = fv_encode_pca(gmm, pca, buf, buf + n * 128, offs.data(), B, 1, fv_out, out_on_device, cuda_stream);
+    std::vector<int64_t> offs(B + 1);
+    for (int b = 0; b <= B; ++b) offs[b] = (int64_t)b * p.ndesc;
+    if (is_bf16(gmm->prec)) {
+        // BF16 form: the PCA projection assembles and normalises each descriptor
+        // from the y-pass buffer itself; only the positions are written here
+        const size_t lat = lattice_floats(p, B);
+        if (rc == FV_OK) {
+            cudaError_t e = cudaMallocAsync((void **)&buf, sizeof(float) * (lat + n * 2), st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "fv_encode_images: cudaMallocAsync(scratch)");
+        }
+        float *xy = buf ? buf + lat : nullptr;
+        if (rc == FV_OK) {
+            cudaError_t e = run_lattice(d, B, H, W, p, buf, st);
+            if (e == cudaSuccess) {
+                KernelTimer kt_("dsift_xy", st);
+                dsift_xy_kernel<<<dim3((unsigned)((p.ndesc + 255) / 256), (unsigned)B), 256, 0, st>>>(p, xy);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess) rc = cuda_fail(e, "fv_encode_images: dense SIFT launch");
+        }
+        if (rc == FV_OK)
+            rc = encode_pca_impl(gmm, pca, nullptr, xy, offs.data(), B, 1, fv_out, out_on_device, cuda_stream,
+                                 lattice_yp(buf, p, B), &p);
+    } else {
+        if (rc == FV_OK) {
+            cudaError_t e = cudaMallocAsync((void **)&buf, sizeof(float) * n * 130, st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "fv_encode_images: cudaMallocAsync(descriptors)");
+        }
+        if (rc == FV_OK) rc = run_dsift(d, B, H, W, p, buf, buf + n * 128, st);
+        if (rc == FV_OK)
+            rc = fv_encode_pca(gmm, pca, buf, buf + n * 128, offs.data(), B, 1, fv_out, out_on_device, cuda_stream);
     }
     if (buf) cudaFreeAsync(buf, st);
     if (owned) cudaFreeAsync(owned, st);

@@ -182,8 +182,16 @@ cudaError_t launch_slot_reduce(const fv_gmm *g, float *part, int P, const FrameI
 // PCA projection + position append (Sec. 3.1) of N rows into device Y:
 // FP32 rows of pitch D (bf16 = false) or bfloat16 rows of pitch ld (bf16 =
 // true, ld a multiple of 16); err: device word set if an MMA wait expired.
+// yp / dsp (BF16 form, Din = 128): the rows are dense-SIFT descriptors
+// assembled from the y-pass buffer yp of plan dsp instead of read from X.
+struct DsPlan;
 cudaError_t launch_pca(const fv_pca *p, const float *X, const float *xy, int64_t N, bool bf16, void *Y, int ld,
-                       uint32_t *err, cudaStream_t st);
+                       uint32_t *err, cudaStream_t st, const float *yp = nullptr, const DsPlan *dsp = nullptr);
+// fv_encode_pca, or (yp != nullptr) the same on rows gathered from a dense-SIFT
+// y-pass buffer (BF16 form, device memory, offsets = B frames of dsp->ndesc).
+int encode_pca_impl(const fv_gmm *gmm, const fv_pca *pca, const float *X, const float *xy, const int64_t *offsets,
+                    int B, int x_on_device, float *fv_out, int out_on_device, void *cuda_stream, const float *yp,
+                    const DsPlan *dsp);
 cudaError_t launch_finalize(const fv_gmm *g, float *part, int P,
                             const FrameInfo *frames, int B, double *sq, float *out, cudaStream_t st,
                             const uint32_t *err = nullptr, const int *B_dev = nullptr, int max_slots = 1,

@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "fv_dsift.h"
 #include "fv_internal.h"
 #include "fv_sm100.cuh"
 
@@ -70,11 +71,37 @@ __global__ void pca_bimg_kernel(const float *__restrict__ P, int m, int Din, int
     }
 }
 
+// GATHER: the 8 values of bin `bin` (entries 8 bin .. 8 bin + 7) of dense-SIFT
+// descriptor `row` (frames of dp.ndesc descriptors), read from the y-pass
+// buffer before normalisation: bin (bx, by) of the descriptor at grid point
+// (ix, iy) is lattice point (iy + by b/S, ix + bx b/S).
+__device__ __forceinline__ void ds_gather(float (&v)[8], int64_t row, int bin, const float *__restrict__ yp,
+                                          const DsPlan &dp) {
+    const int64_t f = row / dp.ndesc, i = row - f * dp.ndesc;
+    int j = 0;
+#pragma unroll 1
+    for (int q = 1; q < dp.n; ++q)
+        if (i >= dp.s[q].desc_off) j = q;
+    const DsScale &c = dp.s[j];
+    const int64_t k = i - c.desc_off;
+    const int iy = (int)(k / c.nx), ix = (int)(k - (int64_t)iy * c.nx);
+    const int bs = dp.b / dp.S;
+    const int mm = iy + (bin >> 2) * bs, t = ix + (bin & 3) * bs;
+    const float4 *src = reinterpret_cast<const float4 *>(yp + (size_t)f * dp.yp + c.yp_off + ((size_t)mm * c.Tx + t) * 8);
+    const float4 a = src[0], b = src[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
 // grid ceil(N / 128), block 256, dynamic smem = basis image + A image.
+// GATHER (Din = 128): row r is dense-SIFT descriptor r, assembled from the
+// y-pass buffer yp (plan dp) and normalised here (L2, cap 0.2, L2; the 16
+// chunks of a row sit in 16 consecutive lanes) instead of being read from X.
+template <bool GATHER>
 __global__ void __launch_bounds__(kPcaThreads)
 pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__restrict__ mean,
                 const uint16_t *__restrict__ bimg, int Npad, int m, const float *__restrict__ xy,
-                uint16_t *__restrict__ Y, int ld, uint32_t *__restrict__ err) {
+                uint16_t *__restrict__ Y, int ld, uint32_t *__restrict__ err, const float *__restrict__ yp,
+                const DsPlan dp) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int nkb = Din / 16;
     const uint32_t b_bytes = 2u * nkb * Npad * 32u;        // [hi | lo] basis image
@@ -106,7 +133,36 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
         const int r = c / (Din / 8), k0 = (c % (Din / 8)) * 8;
         const int64_t row = row0 + r;
         float v[8];
-        if (row < N) {
+        if constexpr (GATHER) {
+            // every lane takes part in the half-warp reductions (rows past N are zeros)
+            if (row < N) {
+                ds_gather(v, row, k0 / 8, yp, dp);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = 0.f;
+            }
+            float ss = 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) ss = fmaf(v[e], v[e], ss);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const float inv = ss > 0.f ? 1.f / sqrtf(ss) : 0.f;
+            float s2 = 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                v[e] = fminf(v[e] * inv, 0.2f);
+                s2 = fmaf(v[e], v[e], s2);
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            const float inv2 = s2 > 0.f ? 1.f / sqrtf(s2) : 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] *= inv2;
+            if (row < N) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] -= mean[k0 + e];
+            }
+        } else if (row < N) {
             const float4 a = *reinterpret_cast<const float4 *>(X + row * Din + k0);
             const float4 b = *reinterpret_cast<const float4 *>(X + row * Din + k0 + 4);
             v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
@@ -283,7 +339,7 @@ size_t bf16_smem(const fv_pca *p) {   // basis image, rows image, mbarrier and T
 // Project N rows into Y (device): FP32 rows of pitch D (bf16 = false) or
 // bfloat16 rows of pitch ld (bf16 = true). err: device word (BF16 form).
 cudaError_t launch_pca(const fv_pca *p, const float *X, const float *xy, int64_t N, bool bf16, void *Y, int ld,
-                       uint32_t *err, cudaStream_t st) {
+                       uint32_t *err, cudaStream_t st, const float *yp, const DsPlan *dsp) {
     if (N <= 0) return cudaSuccess;
     if (!bf16) {
         const size_t smem = sizeof(float) * (size_t)(kF32Rows + 80) * (p->Din + 1);
@@ -295,12 +351,16 @@ cudaError_t launch_pca(const fv_pca *p, const float *X, const float *xy, int64_t
         return cudaGetLastError();
     }
     const size_t smem = bf16_smem(p);
-    cudaError_t e = cudaFuncSetAttribute(pca_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool gather = yp != nullptr;
+    if (gather && (p->Din != 128 || !dsp)) return cudaErrorInvalidValue;
+    auto kern = gather ? pca_bf16_kernel<true> : pca_bf16_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    const DsPlan none{};
     {
         KernelTimer kt_("pca_bf16", st);
-        pca_bf16_kernel<<<(unsigned)((N + kPcaRows - 1) / kPcaRows), kPcaThreads, smem, st>>>(
-            X, N, p->Din, p->mean, p->bimg, p->Npad, p->m, xy, (uint16_t *)Y, ld, err);
+        kern<<<(unsigned)((N + kPcaRows - 1) / kPcaRows), kPcaThreads, smem, st>>>(
+            X, N, p->Din, p->mean, p->bimg, p->Npad, p->m, xy, (uint16_t *)Y, ld, err, yp, gather ? *dsp : none);
     }
     return cudaGetLastError();
 }
