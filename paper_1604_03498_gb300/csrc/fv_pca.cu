@@ -125,22 +125,36 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
         tmem_alloc(&tslot, ncols);
         tmem_relinquish();
     }
+    // GATHER: a thread's 8 chunks (rows tid/16 + 16u, bin tid % 16) are all
+    // requested before the basis copy and before any is converted, then each
+    // row is normalised across the 16 lanes that hold it
+    constexpr int kGItems = kPcaRows * 16 / kPcaThreads;
+    static_assert(kPcaRows * 16 % kPcaThreads == 0 && kPcaThreads % 32 == 0, "whole rows per half-warp");
+    float gv[GATHER ? kGItems : 1][8];
+    if constexpr (GATHER) {
+#pragma unroll
+        for (int u = 0; u < kGItems; ++u) {
+            const int c = threadIdx.x + u * kPcaThreads;
+            const int64_t row = row0 + c / 16;
+            if (row < N) {
+                ds_gather(gv[u], row, c % 16, yp, dp);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) gv[u][e] = 0.f;
+            }
+        }
+    }
     // the basis image (built once per load, L2-resident) into shared memory
     for (uint32_t c = threadIdx.x; c < b_bytes / 16; c += kPcaThreads)
         reinterpret_cast<uint4 *>(sB)[c] = reinterpret_cast<const uint4 *>(bimg)[c];
-    // centred rows split into hi + lo, 8 columns per step
-    for (int c = threadIdx.x; c < kPcaRows * (Din / 8); c += kPcaThreads) {
-        const int r = c / (Din / 8), k0 = (c % (Din / 8)) * 8;
-        const int64_t row = row0 + r;
-        float v[8];
-        if constexpr (GATHER) {
-            // every lane takes part in the half-warp reductions (rows past N are zeros)
-            if (row < N) {
-                ds_gather(v, row, k0 / 8, yp, dp);
-            } else {
+    if constexpr (GATHER) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = 0.f;
-            }
+        for (int u = 0; u < kGItems; ++u) {
+            const int c = threadIdx.x + u * kPcaThreads;
+            const int r = c / 16, k0 = (c % 16) * 8;
+            const int64_t row = row0 + r;
+            float *v = gv[u];
+            // every lane takes part in the half-warp reductions (rows past N are zeros)
             float ss = 0.f;
 #pragma unroll
             for (int e = 0; e < 8; ++e) ss = fmaf(v[e], v[e], ss);
@@ -162,27 +176,46 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v[e] -= mean[k0 + e];
             }
-        } else if (row < N) {
-            const float4 a = *reinterpret_cast<const float4 *>(X + row * Din + k0);
-            const float4 b = *reinterpret_cast<const float4 *>(X + row * Din + k0 + 4);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            uint32_t hw[4], lw[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] -= mean[k0 + e];
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+            for (int e = 0; e < 4; ++e) {
+                const uint16_t h0 = bf16_rn(v[2 * e]), h1 = bf16_rn(v[2 * e + 1]);
+                const uint16_t l0 = bf16_rn(v[2 * e] - bf16_val(h0)), l1 = bf16_rn(v[2 * e + 1] - bf16_val(h1));
+                hw[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                lw[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+            const uint32_t off = sw32_offset(r, k0, kPcaRows);
+            *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(sA + a_term + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-        uint32_t hw[4], lw[4];
+    } else {
+        // centred rows split into hi + lo, 8 columns per step
+        for (int c = threadIdx.x; c < kPcaRows * (Din / 8); c += kPcaThreads) {
+            const int r = c / (Din / 8), k0 = (c % (Din / 8)) * 8;
+            const int64_t row = row0 + r;
+            float v[8];
+            if (row < N) {
+                const float4 a = *reinterpret_cast<const float4 *>(X + row * Din + k0);
+                const float4 b = *reinterpret_cast<const float4 *>(X + row * Din + k0 + 4);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint16_t h0 = bf16_rn(v[2 * e]), h1 = bf16_rn(v[2 * e + 1]);
-            const uint16_t l0 = bf16_rn(v[2 * e] - bf16_val(h0)), l1 = bf16_rn(v[2 * e + 1] - bf16_val(h1));
-            hw[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            lw[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                for (int e = 0; e < 8; ++e) v[e] -= mean[k0 + e];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = 0.f;
+            }
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint16_t h0 = bf16_rn(v[2 * e]), h1 = bf16_rn(v[2 * e + 1]);
+                const uint16_t l0 = bf16_rn(v[2 * e] - bf16_val(h0)), l1 = bf16_rn(v[2 * e + 1] - bf16_val(h1));
+                hw[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                lw[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+            const uint32_t off = sw32_offset(r, k0, kPcaRows);
+            *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(sA + a_term + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-        const uint32_t off = sw32_offset(r, k0, kPcaRows);
-        *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4 *>(sA + a_term + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
     fence_proxy_async_smem();   // generic-proxy stores visible to the MMAs
     tc_fence_before();
