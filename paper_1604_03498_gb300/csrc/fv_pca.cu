@@ -107,11 +107,18 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
     const uint32_t b_bytes = 2u * nkb * Npad * 32u;        // [hi | lo] basis image
     const uint32_t a_term = (uint32_t)nkb * kPcaRows * 32u;
     uint8_t *sB = smem, *sA = smem + b_bytes;
-    uint64_t &bar = *reinterpret_cast<uint64_t *>(sA + 2 * a_term);
-    uint32_t &tslot = *reinterpret_cast<uint32_t *>(sA + 2 * a_term + 8);
+    uint64_t &bar = *reinterpret_cast<uint64_t *>(sA + 2 * a_term);       // MMAs complete
+    uint64_t &lbar = *reinterpret_cast<uint64_t *>(sA + 2 * a_term + 8);  // bulk copies landed
+    uint32_t &tslot = *reinterpret_cast<uint32_t *>(sA + 2 * a_term + 16);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * kPcaRows;
+    const int nrows = (int)min((int64_t)kPcaRows, N - row0);
     const uint32_t ncols = Npad <= 32 ? 32u : (Npad <= 64 ? 64u : 128u);
+    // X rows (pitch Din) of a tile are contiguous: with Din <= 128 (a thread
+    // then holds its whole share of the tile in registers) one bulk copy lands
+    // them, FP32, where the A image goes, and they are read out before the
+    // image is written over them
+    const bool bulk = !GATHER && Din <= 128 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
 
     if ((smem_u32(smem) & 1023u) != 0u) {   // swizzle atoms need aligned blocks (same in every CTA)
         if (threadIdx.x == 0) atomicOr(err, kErrAlign);
@@ -119,18 +126,24 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
     }
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&lbar, 1);
         fence_mbar_init();
+        const uint32_t xbytes = bulk ? (uint32_t)nrows * (uint32_t)Din * 4u : 0u;
+        mbar_arrive_expect_tx(&lbar, b_bytes + xbytes);
+        bulk_g2s(sB, bimg, b_bytes, &lbar);   // the basis image (built at load, L2-resident)
+        if (bulk) bulk_g2s(sA, X + row0 * Din, xbytes, &lbar);
     }
     if (warp == 0) {
         tmem_alloc(&tslot, ncols);
         tmem_relinquish();
     }
-    // GATHER: a thread's 8 chunks (rows tid/16 + 16u, bin tid % 16) are all
-    // requested before the basis copy and before any is converted, then each
-    // row is normalised across the 16 lanes that hold it
+    // a thread's chunks of 8 columns: c = tid + 256 u, row c / (Din / 8),
+    // columns 8 (c % (Din / 8)) ..; all of them are requested before any is
+    // converted (GATHER: rows tid / 16 + 16 u, bin tid % 16, each row then
+    // normalised across the 16 lanes that hold it)
     constexpr int kGItems = kPcaRows * 16 / kPcaThreads;
     static_assert(kPcaRows * 16 % kPcaThreads == 0 && kPcaThreads % 32 == 0, "whole rows per half-warp");
-    float gv[GATHER ? kGItems : 1][8];
+    float gv[kGItems][8];
     if constexpr (GATHER) {
 #pragma unroll
         for (int u = 0; u < kGItems; ++u) {
@@ -144,16 +157,35 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
             }
         }
     }
-    // the basis image (built once per load, L2-resident) into shared memory
-    for (uint32_t c = threadIdx.x; c < b_bytes / 16; c += kPcaThreads)
-        reinterpret_cast<uint4 *>(sB)[c] = reinterpret_cast<const uint4 *>(bimg)[c];
+    // the bulk copies have landed (bounded, about two seconds; on expiry the
+    // tile is computed from whatever shared memory holds and flagged)
+    {
+        bool ok = mbar_try_wait(&lbar, 0);
+        const long long t0 = clock64();
+        while (!ok && clock64() - t0 < 4000000000ll) ok = mbar_try_wait_sleep(&lbar, 0, 2000u);
+        if (!ok) atomicOr(err, kErrTimeout);
+    }
+    // hi + lo of 8 centred values into both A planes (swizzled row r, columns k0..k0+7)
+    auto store_split = [&](int r, int k0, const float(&v)[8]) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint16_t h0 = bf16_rn(v[2 * e]), h1 = bf16_rn(v[2 * e + 1]);
+            const uint16_t l0 = bf16_rn(v[2 * e] - bf16_val(h0)), l1 = bf16_rn(v[2 * e + 1] - bf16_val(h1));
+            hw[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            lw[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+        }
+        const uint32_t off = sw32_offset(r, k0, kPcaRows);
+        *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(sA + a_term + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    };
     if constexpr (GATHER) {
 #pragma unroll
         for (int u = 0; u < kGItems; ++u) {
             const int c = threadIdx.x + u * kPcaThreads;
             const int r = c / 16, k0 = (c % 16) * 8;
             const int64_t row = row0 + r;
-            float *v = gv[u];
+            float(&v)[8] = gv[u];
             // every lane takes part in the half-warp reductions (rows past N are zeros)
             float ss = 0.f;
 #pragma unroll
@@ -176,18 +208,32 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v[e] -= mean[k0 + e];
             }
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint16_t h0 = bf16_rn(v[2 * e]), h1 = bf16_rn(v[2 * e + 1]);
-                const uint16_t l0 = bf16_rn(v[2 * e] - bf16_val(h0)), l1 = bf16_rn(v[2 * e + 1] - bf16_val(h1));
-                hw[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                lw[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-            }
-            const uint32_t off = sw32_offset(r, k0, kPcaRows);
-            *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(sA + a_term + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            store_split(r, k0, v);
         }
+    } else if (bulk) {
+        const int per = Din / 8, nit = Din / 16;   // 256 % per == 0: a thread's columns are the same in every chunk
+        const int k0 = (threadIdx.x % per) * 8;
+        float mk[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) mk[e] = mean[k0 + e];
+        const float *sX = reinterpret_cast<const float *>(sA);
+#pragma unroll
+        for (int u = 0; u < kGItems; ++u) {
+            const int r = (threadIdx.x + u * kPcaThreads) / per;
+            if (u < nit && r < nrows) {
+                const float4 a = *reinterpret_cast<const float4 *>(sX + r * Din + k0);
+                const float4 b = *reinterpret_cast<const float4 *>(sX + r * Din + k0 + 4);
+                gv[u][0] = a.x - mk[0]; gv[u][1] = a.y - mk[1]; gv[u][2] = a.z - mk[2]; gv[u][3] = a.w - mk[3];
+                gv[u][4] = b.x - mk[4]; gv[u][5] = b.y - mk[5]; gv[u][6] = b.z - mk[6]; gv[u][7] = b.w - mk[7];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) gv[u][e] = 0.f;
+            }
+        }
+        __syncthreads();   // every staged row is read before the image is written over it
+#pragma unroll
+        for (int u = 0; u < kGItems; ++u)
+            if (u < nit) store_split((threadIdx.x + u * kPcaThreads) / per, k0, gv[u]);
     } else {
         // centred rows split into hi + lo, 8 columns per step
         for (int c = threadIdx.x; c < kPcaRows * (Din / 8); c += kPcaThreads) {
@@ -204,17 +250,7 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v[e] = 0.f;
             }
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint16_t h0 = bf16_rn(v[2 * e]), h1 = bf16_rn(v[2 * e + 1]);
-                const uint16_t l0 = bf16_rn(v[2 * e] - bf16_val(h0)), l1 = bf16_rn(v[2 * e + 1] - bf16_val(h1));
-                hw[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                lw[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-            }
-            const uint32_t off = sw32_offset(r, k0, kPcaRows);
-            *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(sA + a_term + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            store_split(r, k0, v);
         }
     }
     fence_proxy_async_smem();   // generic-proxy stores visible to the MMAs
@@ -294,7 +330,10 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
         }
     }
     // the MMAs are complete before TMEM is released (bounded, also after an expired wait)
-    if (threadIdx.x == 0) mbar_drain(&bar, 0, 2000000000ll);
+    if (threadIdx.x == 0) {
+        mbar_drain(&bar, 0, 2000000000ll);
+        mbar_drain(&lbar, 0, 2000000000ll);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -363,8 +402,8 @@ bool dev_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-size_t bf16_smem(const fv_pca *p) {   // basis image, rows image, mbarrier and TMEM slot
-    return (size_t)2 * (p->Din / 16) * p->Npad * 32 + (size_t)2 * (p->Din / 16) * kPcaRows * 32 + 16;
+size_t bf16_smem(const fv_pca *p) {   // basis image, rows image, two mbarriers and the TMEM slot
+    return (size_t)2 * (p->Din / 16) * p->Npad * 32 + (size_t)2 * (p->Din / 16) * kPcaRows * 32 + 32;
 }
 
 }  // namespace

@@ -10,7 +10,8 @@ absolute terms sum_k |x_k - mean_k| |P_jk|. Encodes: 1e-4 (FP32 form) and 2e-3 (
 given the exact projection rounded to bfloat16) max-abs on the normalised
 vector. Shapes: m = 62 and 78 (D = 64 and 80, the encoder's sizes), m = 48
 (the positions land past the padded projection columns), no positions,
-ragged row counts, host and device inputs."""
+ragged row counts, input widths 16, 64, 128 (tiles landed by one bulk copy)
+and 256 (rows loaded by the threads), host and device inputs."""
 import numpy as np
 import pytest
 
@@ -21,17 +22,19 @@ from paper_1604_03498_gb300 import fv, synth
 pytestmark = pytest.mark.gpu
 
 
-def _inputs(N, m, seed, with_xy=True):
-    X = synth.sample_sift_like(N, 128, seed=seed)
-    P, mean = synth.make_pca(128, m, seed=seed)
+def _inputs(N, m, seed, with_xy=True, Din=128):
+    X = synth.sample_sift_like(N, Din, seed=seed)
+    P, mean = synth.make_pca(Din, m, seed=seed)
     xy = synth.sample_positions(N, seed=seed) if with_xy else None
     return X, P, mean, xy
 
 
-@pytest.mark.parametrize("N,m,with_xy", [(1000, 62, True), (333, 78, True), (129, 48, True), (500, 30, False)])
-def test_projection_fp32_and_bf16_match_the_oracle(N, m, with_xy):
+@pytest.mark.parametrize("N,m,with_xy,Din", [(1000, 62, True, 128), (333, 78, True, 128), (129, 48, True, 128),
+                                             (500, 30, False, 128), (300, 14, True, 16), (385, 40, True, 64),
+                                             (257, 62, True, 256)])
+def test_projection_fp32_and_bf16_match_the_oracle(N, m, with_xy, Din):
     torch = torch_cuda()
-    X, P, mean, xy = _inputs(N, m, 91, with_xy)
+    X, P, mean, xy = _inputs(N, m, 91, with_xy, Din)
     ref = oracle.pca_project(X, P, mean, xy)
     D = ref.shape[1]
     p = fv.fv_pca_load(P, mean)
