@@ -134,6 +134,7 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
         if (bulk) bulk_g2s(sA, X + row0 * Din, xbytes, &lbar);
     }
     if (warp == 0) {
+        __syncwarp();   // the allocation is warp-wide, after thread 0's branch
         tmem_alloc(&tslot, ncols);
         tmem_relinquish();
     }
@@ -157,6 +158,7 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
             }
         }
     }
+    __syncthreads();   // both mbarriers are initialised before any thread waits on one
     // the bulk copies have landed (bounded, about two seconds; on expiry the
     // tile is computed from whatever shared memory holds and flagged)
     {
