@@ -158,6 +158,23 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
             }
         }
     }
+    // requested before the waits: the thread's 8 column means (GATHER and bulk:
+    // 256 is a multiple of Din / 8, so its columns are the same in every chunk)
+    // and the position pair of its epilogue row (lane quadrant warp % 4)
+    const int per = Din / 8, kt0 = (threadIdx.x % per) * 8;
+    float mk[8];
+    if (GATHER || bulk) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) mk[e] = mean[kt0 + e];
+    }
+    const int eq = warp & 3, ehalf = warp >> 2;
+    const int er = eq * 32 + lane;
+    const int64_t erow = row0 + er;
+    float exy0 = 0.f, exy1 = 0.f;
+    if (xy && erow < N) {
+        exy0 = xy[2 * erow];
+        exy1 = xy[2 * erow + 1];
+    }
     __syncthreads();   // both mbarriers are initialised before any thread waits on one
     // the bulk copies have landed (bounded, about two seconds; on expiry the
     // tile is computed from whatever shared memory holds and flagged)
@@ -185,7 +202,7 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
 #pragma unroll
         for (int u = 0; u < kGItems; ++u) {
             const int c = threadIdx.x + u * kPcaThreads;
-            const int r = c / 16, k0 = (c % 16) * 8;
+            const int r = c / 16, k0 = kt0;
             const int64_t row = row0 + r;
             float(&v)[8] = gv[u];
             // every lane takes part in the half-warp reductions (rows past N are zeros)
@@ -208,16 +225,12 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
             for (int e = 0; e < 8; ++e) v[e] *= inv2;
             if (row < N) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] -= mean[k0 + e];
+                for (int e = 0; e < 8; ++e) v[e] -= mk[e];
             }
             store_split(r, k0, v);
         }
     } else if (bulk) {
-        const int per = Din / 8, nit = Din / 16;   // 256 % per == 0: a thread's columns are the same in every chunk
-        const int k0 = (threadIdx.x % per) * 8;
-        float mk[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) mk[e] = mean[k0 + e];
+        const int nit = Din / 16, k0 = kt0;
         const float *sX = reinterpret_cast<const float *>(sA);
 #pragma unroll
         for (int u = 0; u < kGItems; ++u) {
@@ -275,7 +288,8 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
         }
         mma_commit(&bar);
     }
-    if (warp < 4) {
+    {
+        // every warp: its TMEM lane quadrant's rows, 32-column chunks 32 ehalf + 64 j;
         // bounded wait for the MMAs (about two seconds); on expiry the rows become NaN
         bool ok = mbar_try_wait(&bar, 0);
         const long long t0 = clock64();
@@ -283,14 +297,12 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
         ok = __all_sync(0xffffffffu, ok);
         if (!ok && lane == 0) atomicOr(err, kErrTimeout);
         tc_fence_after();
-        const int r = warp * 32 + lane;
-        const int64_t row = row0 + r;
-        uint16_t *yr = Y + row * ld;
-        for (int c0 = 0; c0 < Npad; c0 += 32) {
+        uint16_t *yr = Y + erow * ld;
+        for (int c0 = ehalf * 32; c0 < Npad; c0 += 64) {
             uint32_t v[32];
-            tmem_ld32_issue(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld32_issue(tmem + ((uint32_t)(eq * 32) << 16) + (uint32_t)c0, v);
             tmem_ld_wait(v);
-            if (row < N) {
+            if (erow < N) {
 #pragma unroll
                 for (int e = 0; e < 32; e += 8) {
                     const int n0 = c0 + e;
@@ -304,7 +316,7 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
                             const int n = n0 + 2 * q + t;
                             float f = 0.f;
                             if (n < m) f = ok ? __uint_as_float(v[e + 2 * q + t]) : __int_as_float(0x7fc00000);
-                            else if (xy && n < m + 2) f = xy[2 * row + (n - m)];
+                            else if (n < m + 2) f = n == m ? exy0 : exy1;
                             h[t] = bf16_rn(f);
                         }
                         w4[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
@@ -314,7 +326,7 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
             }
         }
         // columns past Npad (the position pair when m is a multiple of 16, and padding)
-        if (row < N) {
+        if (ehalf == 0 && erow < N) {
             for (int n0 = Npad; n0 < ld; n0 += 8) {
                 uint32_t w4[4];
 #pragma unroll
@@ -323,7 +335,7 @@ pca_bf16_kernel(const float *__restrict__ X, int64_t N, int Din, const float *__
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
                         const int n = n0 + 2 * q + t;
-                        h[t] = bf16_rn((xy && n >= m && n < m + 2) ? xy[2 * row + (n - m)] : 0.f);
+                        h[t] = bf16_rn(n == m ? exy0 : (n == m + 1 ? exy1 : 0.f));
                     }
                     w4[q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
                 }
