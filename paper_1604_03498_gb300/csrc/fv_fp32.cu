@@ -101,7 +101,9 @@ constexpr int P_THREADS = 256;
 // cycles per SM (16), so K <= 256 takes RR = 8 (two blocks per SM, twice the
 // FMAs per load); larger K keeps RR = 4 (three blocks per SM at K <= 256
 // would need it, and 8 rows x 16 components of accumulators do not fit).
-constexpr int R_DS = 8;                // dimension slice
+// dimension slice: 16 dimensions (half as many slice hand-overs) where two
+// stages of it leave room for two blocks per SM, else 8
+__host__ __device__ constexpr int r_ds(int kt) { return kt <= 256 ? 16 : 8; }
 
 template <int CPL, int NC, int RR>
 __global__ void __launch_bounds__(P_THREADS, (CPL * NC <= 8 && RR == 4) ? 3 : 2)
@@ -112,6 +114,7 @@ f32_post_reg_kernel(const float *__restrict__ X, int64_t rows, int D, int Kp, co
     constexpr int KT = KCH * NC;           // all (padded) components
     constexpr int BM = 8 * RR;             // rows per block
     constexpr int XS = BM + 4;
+    constexpr int R_DS = r_ds(KT);
     constexpr int STAGE = 2 * R_DS * KT + R_DS * XS;
     extern __shared__ __align__(16) float smem[];
 
@@ -472,6 +475,7 @@ namespace {
 template <int CPL, int NC, int RR = (CPL * NC <= 8 ? 8 : 4)>
 cudaError_t launch_post_reg(const fv_gmm *g, const float *X, int64_t rows, float *gamma, cudaStream_t st, float *lse) {
     constexpr int KT = 32 * CPL * NC, BM = 8 * RR;
+    constexpr int R_DS = r_ds(KT);
     const size_t smem = sizeof(float) * 2 * (2 * R_DS * KT + R_DS * (BM + 4));
     cudaError_t e = cudaFuncSetAttribute(f32_post_reg_kernel<CPL, NC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
