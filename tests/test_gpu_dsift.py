@@ -37,6 +37,8 @@ def _gpu_dsift(frames, on_device=True, **params):
     (57, 83, {}, False),                                      # odd sizes, host frames
     (120, 160, dict(bin_size=8, stride=4), True),
     (100, 130, dict(bin_size=4, stride=2, n_scales=9, top_scale=2), True),
+    (200, 300, dict(bin_size=16, stride=16), True),           # the widest pixel span of an x-pass block
+    (64, 96, dict(bin_size=2, stride=1), True),               # three 64-column segments per row at the top scale
 ])
 def test_descriptors_match_oracle(H, W, params, on_device):
     frames = synth.make_frames(2, H, W, seed=H + W)
