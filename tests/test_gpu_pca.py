@@ -10,7 +10,7 @@ absolute terms sum_k |x_k - mean_k| |P_jk|. Encodes: 1e-4 (FP32 form) and 2e-3 (
 given the exact projection rounded to bfloat16) max-abs on the normalised
 vector. Shapes: m = 62 and 78 (D = 64 and 80, the encoder's sizes), m = 48
 (the positions land past the padded projection columns), no positions,
-ragged row counts, input widths 16, 64, 128 (tiles landed by one bulk copy)
+ragged row counts (one partial tile, a single row), input widths 16, 64, 128 (tiles landed by one bulk copy)
 and 256 (rows loaded by the threads), host and device inputs."""
 import numpy as np
 import pytest
@@ -31,7 +31,7 @@ def _inputs(N, m, seed, with_xy=True, Din=128):
 
 @pytest.mark.parametrize("N,m,with_xy,Din", [(1000, 62, True, 128), (333, 78, True, 128), (129, 48, True, 128),
                                              (500, 30, False, 128), (300, 14, True, 16), (385, 40, True, 64),
-                                             (257, 62, True, 256)])
+                                             (257, 62, True, 256), (77, 62, True, 128), (1, 62, True, 128)])
 def test_projection_fp32_and_bf16_match_the_oracle(N, m, with_xy, Din):
     torch = torch_cuda()
     X, P, mean, xy = _inputs(N, m, 91, with_xy, Din)
